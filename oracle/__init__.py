@@ -1,0 +1,190 @@
+"""Scalar CPU oracle for the alias-path R-MAT generator (arXiv 1905.03525).
+
+TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` leg of ``bench.py`` are the only users.  The product package
+never imports this module, and this module never imports the product package.
+
+The C source (``rmat_oracle.c``) restates the paper's table construction
+(Sec. 2, table-construction fragment), Walker's alias method (Sec. 2), the
+sampling loop (Sec. 2, sampling-loop fragment), undirected mirroring (Sec. 3)
+and the naive per-bit R-MAT process (Sec. 1), plus Philox4x32-10 (Salmon et
+al., SC'11).  This file only compiles it with gcc and marshals arguments.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rmat_oracle.c")
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD_DIR, "librmat_oracle.so")
+
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/librmat_oracle.so`` (plain gcc,
+    no fast-math, no FMA contraction) and return the library path."""
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    stale = (not os.path.exists(_LIB_PATH)
+             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)
+             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(os.path.join(_HERE, "rmat_oracle.h")))
+    if force or stale:
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+               "-fno-fast-math", "-Wall", "-Wextra", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            u32, u64, i32, dbl = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_double
+            vp = ctypes.c_void_p
+            L.orc_philox4x32_10.argtypes = [vp, vp, vp]
+            L.orc_word.argtypes = [u64, u64, u64]
+            L.orc_word.restype = u32
+            L.orc_table_variable.argtypes = [dbl, dbl, dbl, dbl, i32, u64]
+            L.orc_table_variable.restype = vp
+            L.orc_table_fixed.argtypes = [vp, i32]
+            L.orc_table_fixed.restype = vp
+            L.orc_table_free.argtypes = [vp]
+            for name in ("orc_table_entries", "orc_table_bits", "orc_table_max_len"):
+                getattr(L, name).argtypes = [vp]
+                getattr(L, name).restype = i32
+            L.orc_table_get.argtypes = [vp] * 7
+            L.orc_draw.argtypes = [vp, u32]
+            L.orc_draw.restype = u32
+            L.orc_generate.argtypes = [vp, i32, i32, i32, u64, u64, u64, vp, vp]
+            L.orc_generate.restype = i32
+            L.orc_generate_naive.argtypes = [vp, i32, i32, u64, u64, u64, vp, vp]
+            L.orc_generate_naive.restype = i32
+            L.orc_edge_distribution.argtypes = [vp, i32, i32, i32, vp]
+            L.orc_edge_distribution.restype = i32
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def word(seed: int, e: int, n: int) -> int:
+    return int(lib().orc_word(seed, e, n))
+
+
+class Table:
+    """One oracle alias table (a single table, or one level group)."""
+
+    def __init__(self, handle):
+        if not handle:
+            raise ValueError("oracle rejected the table arguments")
+        self._h = ctypes.c_void_p(handle)
+        L = lib()
+        self.entries = L.orc_table_entries(self._h)
+        self.bits = L.orc_table_bits(self._h)
+        self.max_len = L.orc_table_max_len(self._h)
+        N = 1 << self.bits
+        self.sym = np.zeros(N, np.uint64)
+        self.len = np.zeros(N, np.uint8)
+        self.p = np.zeros(N, np.float64)
+        self.w = np.zeros(N, np.uint64)
+        self.thr = np.zeros(N, np.uint32)
+        self.alias = np.zeros(N, np.uint32)
+        L.orc_table_get(self._h, _ptr(self.sym), _ptr(self.len), _ptr(self.p), _ptr(self.w),
+                        _ptr(self.thr), _ptr(self.alias))
+
+    @classmethod
+    def variable(cls, a, b, c, d, k, bound):
+        return cls(lib().orc_table_variable(a, b, c, d, k, bound))
+
+    @classmethod
+    def fixed(cls, P, ell=None):
+        P = np.ascontiguousarray(P, dtype=np.float64).reshape(-1, 4)
+        if ell is None:
+            ell = P.shape[0]
+        if P.shape[0] == 1 and ell > 1:
+            P = np.repeat(P, ell, axis=0)
+        return cls(lib().orc_table_fixed(_ptr(P), ell))
+
+    def draw(self, u: int) -> int:
+        return int(lib().orc_draw(self._h, u))
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None):
+                lib().orc_table_free(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+
+def _handles(tables):
+    arr = (ctypes.c_void_p * len(tables))(*[t._h.value for t in tables])
+    return arr
+
+
+def generate(tables, k, seed, e0, count, undirected=False):
+    """Edges e0 .. e0+count-1 as (row, col) uint64 arrays."""
+    tables = list(tables)
+    row = np.zeros(count, np.uint64)
+    col = np.zeros(count, np.uint64)
+    h = _handles(tables)
+    rc = lib().orc_generate(h, len(tables), k, int(undirected), seed, e0, count, _ptr(row), _ptr(col))
+    if rc != 0:
+        raise ValueError("oracle rejected the generate arguments")
+    return row, col
+
+
+def generate_naive(P_levels, k, seed, e0, count, undirected=False):
+    P = np.ascontiguousarray(P_levels, dtype=np.float64).reshape(-1, 4)
+    if P.shape[0] == 1:
+        P = np.repeat(P, k, axis=0)
+    row = np.zeros(count, np.uint64)
+    col = np.zeros(count, np.uint64)
+    rc = lib().orc_generate_naive(_ptr(P), k, int(undirected), seed, e0, count, _ptr(row), _ptr(col))
+    if rc != 0:
+        raise ValueError("oracle rejected the naive arguments")
+    return row, col
+
+
+def edge_distribution(tables, k, quantised=False) -> np.ndarray:
+    """Exact P(row, col) as a 2^k x 2^k array."""
+    tables = list(tables)
+    out = np.zeros((1 << k) * (1 << k), np.float64)
+    rc = lib().orc_edge_distribution(_handles(tables), len(tables), k, int(quantised), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle rejected the distribution arguments")
+    return out.reshape(1 << k, 1 << k)
+
+
+def level_groups(P_levels, k, ell):
+    """Fixed-length tables for consecutive groups of ell levels (the last group
+    holds the remaining k mod ell levels), level t using P_levels[t]."""
+    P = np.ascontiguousarray(P_levels, dtype=np.float64).reshape(-1, 4)
+    if P.shape[0] == 1:
+        P = np.repeat(P, k, axis=0)
+    tables = []
+    for g0 in range(0, k, ell):
+        n = min(ell, k - g0)
+        tables.append(Table.fixed(P[g0:g0 + n], n))
+    return tables

@@ -1,0 +1,478 @@
+/*
+ * rmat_oracle.c -- scalar CPU oracle for the alias-path R-MAT generator
+ * (Huebschle-Schneider & Sanders, arXiv 1905.03525).
+ *
+ * TEST INFRASTRUCTURE ONLY: used by the tests, the smoke check and the
+ * benchmark's CPU-baseline leg; never by the product path.  It is written to
+ * be read against the paper, not to be fast: one edge at a time, one level at
+ * a time, FP64 for probabilities and exact integers everywhere else.
+ *
+ * Readings of the paper that the code follows (the paper is silent or
+ * garbled on these points; the CUDA library makes the same choices):
+ *   R1  stop rule of the table-construction fragment: expand while
+ *       |Q| + 3 < bound (this reproduces the table sizes of Fig. 1:
+ *       bound 2^12 -> 4093 entries).
+ *   R2  ties in deleteMax: larger p first, then the lexicographically
+ *       smaller symbol string.
+ *   R3  entries whose path already has min(k, 32) levels are not expanded.
+ *   R4  canonical entry order = lexicographic order of the symbol strings;
+ *       the table is padded with zero-probability entries to N = 2^b.
+ *   R5  p -> u32 weights w with sum 2^32: floor(p 2^32), remainder to the
+ *       largest fractional parts (ties to the lower index).
+ *   R6  integer Vose alias table with FIFO small/large lists.
+ *   R7  one 32-bit Philox word per draw: top b bits = column, low 32-b bits
+ *       compared with the column threshold.
+ *   R8  bits left over after k levels are dropped (the sampling-loop fragment
+ *       carries them to the next edge; keying the stream per edge makes every
+ *       edge independent of the others instead).
+ *   R9  the four parameters are divided by their sum before use.
+ */
+#include "rmat_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as  */
+/* easy as 1, 2, 3", SC'11).  Round: two 32x32->64 products of the even     */
+/* counter words with the round multipliers; the new words are the high     */
+/* halves xored with the odd words and the round key, and the low halves.   */
+/* The key is bumped by the Weyl constants between rounds.                  */
+/* ------------------------------------------------------------------ */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t prod0 = (uint64_t)PHILOX_M0 * (uint64_t)x0;
+        uint64_t prod1 = (uint64_t)PHILOX_M1 * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+        k0 += PHILOX_W0;
+        k1 += PHILOX_W1;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+uint32_t orc_word(uint64_t seed, uint64_t e, uint64_t n)
+{
+    uint64_t q = n / 4;
+    uint32_t ctr[4] = {(uint32_t)q, (uint32_t)(q >> 32), (uint32_t)e, (uint32_t)(e >> 32)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return out[n % 4];
+}
+
+/* ------------------------------------------------------------------ */
+/* Tables                                                              */
+/* ------------------------------------------------------------------ */
+struct orc_table {
+    int entries;    /* |Q| */
+    int bits;       /* b, N = 2^b */
+    int max_len;
+    uint64_t *sym;  /* N symbol strings, first level in bits 63..62 */
+    uint8_t *len;   /* N path lengths (levels) */
+    double *p;      /* N path probabilities */
+    uint64_t *w;    /* N quantised weights, sum 2^32 */
+    uint32_t *thr;  /* N alias thresholds */
+    uint32_t *alias;/* N alias targets */
+};
+
+static int symbol_at(uint64_t sym, int t) { return (int)((sym >> (62 - 2 * t)) & 3u); }
+
+static int normalise(const double in[4], double out[4])
+{
+    for (int i = 0; i < 4; ++i)
+        if (!(in[i] >= 0.0) || !isfinite(in[i])) return -1;
+    double s = ((in[0] + in[1]) + in[2]) + in[3];
+    if (!(fabs(s - 1.0) <= 1e-9)) return -1;
+    for (int i = 0; i < 4; ++i) out[i] = in[i] / s;
+    return 0;
+}
+
+/* Entry of Q while the table-construction fragment runs. */
+typedef struct { double p; uint64_t sym; int len; } qentry;
+
+/* Is x to be expanded before y?  Larger p first; equal p: lexicographically
+ * smaller symbol string first (reading R2).  Entries of Q never are prefixes
+ * of each other, so comparing the left-aligned strings is lexicographic. */
+static int q_before(const qentry *x, const qentry *y)
+{
+    if (x->p != y->p) return x->p > y->p;
+    return x->sym < y->sym;
+}
+
+/* Binary max-heap on q_before. */
+typedef struct { qentry *v; size_t n, cap; } qheap;
+
+static int heap_push(qheap *h, qentry e)
+{
+    if (h->n == h->cap) {
+        size_t nc = h->cap ? 2 * h->cap : 64;
+        qentry *nv = (qentry *)realloc(h->v, nc * sizeof(qentry));
+        if (!nv) return -1;
+        h->v = nv; h->cap = nc;
+    }
+    size_t i = h->n++;
+    h->v[i] = e;
+    while (i > 0) {
+        size_t parent = (i - 1) / 2;
+        if (!q_before(&h->v[i], &h->v[parent])) break;
+        qentry tmp = h->v[i]; h->v[i] = h->v[parent]; h->v[parent] = tmp;
+        i = parent;
+    }
+    return 0;
+}
+
+static qentry heap_pop(qheap *h)
+{
+    qentry top = h->v[0];
+    h->v[0] = h->v[--h->n];
+    size_t i = 0;
+    for (;;) {
+        size_t l = 2 * i + 1, r = l + 1, best = i;
+        if (l < h->n && q_before(&h->v[l], &h->v[best])) best = l;
+        if (r < h->n && q_before(&h->v[r], &h->v[best])) best = r;
+        if (best == i) break;
+        qentry tmp = h->v[i]; h->v[i] = h->v[best]; h->v[best] = tmp;
+        i = best;
+    }
+    return top;
+}
+
+static int cmp_sym(const void *x, const void *y)
+{
+    const qentry *a = (const qentry *)x, *b = (const qentry *)y;
+    return (a->sym > b->sym) - (a->sym < b->sym);
+}
+
+/* Sort key for the largest-remainder step: fractional part desc, index asc. */
+typedef struct { double frac; int idx; } fracidx;
+
+static int cmp_frac(const void *x, const void *y)
+{
+    const fracidx *a = (const fracidx *)x, *b = (const fracidx *)y;
+    if (a->frac != b->frac) return (a->frac < b->frac) - (a->frac > b->frac);
+    return (a->idx > b->idx) - (a->idx < b->idx);
+}
+
+static orc_table *table_alloc(int entries)
+{
+    int bits = 0;
+    while ((1LL << bits) < entries) ++bits;
+    if (bits < 1) bits = 1;
+    size_t N = (size_t)1 << bits;
+    orc_table *t = (orc_table *)calloc(1, sizeof(orc_table));
+    if (!t) return NULL;
+    t->entries = entries;
+    t->bits = bits;
+    t->sym = (uint64_t *)calloc(N, sizeof(uint64_t));
+    t->len = (uint8_t *)calloc(N, sizeof(uint8_t));
+    t->p = (double *)calloc(N, sizeof(double));
+    t->w = (uint64_t *)calloc(N, sizeof(uint64_t));
+    t->thr = (uint32_t *)calloc(N, sizeof(uint32_t));
+    t->alias = (uint32_t *)calloc(N, sizeof(uint32_t));
+    if (!t->sym || !t->len || !t->p || !t->w || !t->thr || !t->alias) {
+        orc_table_free(t);
+        return NULL;
+    }
+    return t;
+}
+
+/* Quantisation (reading R5) and integer Vose alias construction (R6,
+ * Walker's alias method as used in Sec. 2). */
+static int quantise_and_alias(orc_table *t)
+{
+    int N = 1 << t->bits;
+    uint64_t C = (uint64_t)1 << (32 - t->bits);
+    const uint64_t total = (uint64_t)1 << 32;
+
+    /* w_i = floor(p_i 2^32); the scaling by 2^32 is exact in FP64. */
+    uint64_t sum = 0;
+    fracidx *fr = (fracidx *)malloc((size_t)N * sizeof(fracidx));
+    if (!fr) return -1;
+    for (int i = 0; i < N; ++i) {
+        double x = ldexp(t->p[i], 32);
+        double fl = floor(x);
+        t->w[i] = (uint64_t)fl;
+        fr[i].frac = x - fl;
+        fr[i].idx = i;
+        sum += t->w[i];
+    }
+    if (sum > total) { free(fr); return -1; }
+    uint64_t delta = total - sum;
+    if (delta > (uint64_t)N) { free(fr); return -1; }
+    qsort(fr, (size_t)N, sizeof(fracidx), cmp_frac);
+    for (uint64_t r = 0; r < delta; ++r) t->w[fr[r].idx] += 1;
+    free(fr);
+
+    /* Vose: small = {i : w_i < C}, large = {i : w_i >= C}, both FIFO in
+     * ascending index order. */
+    uint64_t *rest = (uint64_t *)malloc((size_t)N * sizeof(uint64_t));
+    int *small = (int *)malloc((size_t)N * sizeof(int));
+    int *large = (int *)malloc((size_t)N * sizeof(int));
+    if (!rest || !small || !large) { free(rest); free(small); free(large); return -1; }
+    int s_head = 0, s_tail = 0, l_head = 0, l_tail = 0;
+    for (int i = 0; i < N; ++i) {
+        rest[i] = t->w[i];
+        if (rest[i] < C) small[s_tail++] = i;
+        else large[l_tail++] = i;
+    }
+    while (s_head < s_tail && l_head < l_tail) {
+        int s = small[s_head++];
+        int l = large[l_head];
+        t->thr[s] = (uint32_t)rest[s];
+        t->alias[s] = (uint32_t)l;
+        rest[l] -= C - rest[s];
+        if (rest[l] < C) {
+            l_head++;
+            small[s_tail++] = l;   /* each index enters small at most once */
+        }
+    }
+    int ok = (s_head == s_tail);
+    while (l_head < l_tail) {
+        int l = large[l_head++];
+        t->thr[l] = (uint32_t)(C - 1);
+        t->alias[l] = (uint32_t)l;
+    }
+    free(rest); free(small); free(large);
+    return ok ? 0 : -1;
+}
+
+orc_table *orc_table_variable(double a, double b, double c, double d, int k, uint64_t bound)
+{
+    double in[4] = {a, b, c, d}, P[4];
+    if (normalise(in, P) != 0) return NULL;
+    if (k < 1 || k > 64 || bound < 5 || bound > ((uint64_t)1 << 24)) return NULL;
+    int cap = k < 32 ? k : 32;
+
+    /* Q starts as the empty path with probability 1.  Entries that reached
+     * the depth cap leave the heap for `done` (reading R3). */
+    qheap heap = {0};
+    qentry *done = (qentry *)malloc((size_t)bound * sizeof(qentry));
+    if (!done) return NULL;
+    size_t ndone = 0;
+    qentry root = {1.0, 0, 0};
+    if (heap_push(&heap, root) != 0) { free(done); return NULL; }
+    /* Reading R1: expand while |Q| + 3 < bound. */
+    while (heap.n > 0 && heap.n + ndone + 3 < bound) {
+        qentry e = heap_pop(&heap);
+        for (int s = 0; s < 4; ++s) {
+            qentry child;
+            child.p = e.p * P[s];
+            child.len = e.len + 1;
+            child.sym = e.sym | ((uint64_t)s << (62 - 2 * e.len));
+            if (child.len >= cap) done[ndone++] = child;
+            else if (heap_push(&heap, child) != 0) { free(heap.v); free(done); return NULL; }
+        }
+    }
+    int entries = (int)(heap.n + ndone);
+    qentry *all = (qentry *)malloc((size_t)entries * sizeof(qentry));
+    if (!all) { free(heap.v); free(done); return NULL; }
+    memcpy(all, done, ndone * sizeof(qentry));
+    memcpy(all + ndone, heap.v, heap.n * sizeof(qentry));
+    free(heap.v); free(done);
+
+    /* Reading R4: lexicographic order of the symbol strings. */
+    qsort(all, (size_t)entries, sizeof(qentry), cmp_sym);
+
+    orc_table *t = table_alloc(entries);
+    if (!t) { free(all); return NULL; }
+    for (int i = 0; i < entries; ++i) {
+        t->sym[i] = all[i].sym;
+        t->len[i] = (uint8_t)all[i].len;
+        t->p[i] = all[i].p;
+        if (all[i].len > t->max_len) t->max_len = all[i].len;
+    }
+    free(all);
+    if (quantise_and_alias(t) != 0) { orc_table_free(t); return NULL; }
+    return t;
+}
+
+orc_table *orc_table_fixed(const double *Pin, int ell)
+{
+    if (ell < 1 || ell > 12) return NULL;
+    double *P = (double *)malloc((size_t)ell * 4 * sizeof(double));
+    if (!P) return NULL;
+    for (int t = 0; t < ell; ++t)
+        if (normalise(Pin + 4 * t, P + 4 * t) != 0) { free(P); return NULL; }
+    int entries = 1 << (2 * ell);
+    orc_table *t = table_alloc(entries);
+    if (!t) { free(P); return NULL; }
+    t->max_len = ell;
+    /* Entry i is the path whose symbols are the base-4 digits of i, first
+     * level = most significant digit; p is the product of the level
+     * parameters taken from the top level down. */
+    for (int i = 0; i < entries; ++i) {
+        uint64_t sym = 0;
+        double p = 1.0;
+        for (int lvl = 0; lvl < ell; ++lvl) {
+            int s = (i >> (2 * (ell - 1 - lvl))) & 3;
+            sym |= (uint64_t)s << (62 - 2 * lvl);
+            p = p * P[4 * lvl + s];
+        }
+        t->sym[i] = sym;
+        t->len[i] = (uint8_t)ell;
+        t->p[i] = p;
+    }
+    free(P);
+    if (quantise_and_alias(t) != 0) { orc_table_free(t); return NULL; }
+    return t;
+}
+
+void orc_table_free(orc_table *t)
+{
+    if (!t) return;
+    free(t->sym); free(t->len); free(t->p); free(t->w); free(t->thr); free(t->alias);
+    free(t);
+}
+
+int orc_table_entries(const orc_table *t) { return t->entries; }
+int orc_table_bits(const orc_table *t) { return t->bits; }
+int orc_table_max_len(const orc_table *t) { return t->max_len; }
+
+void orc_table_get(const orc_table *t, uint64_t *sym, uint8_t *len, double *p,
+                   uint64_t *w, uint32_t *thr, uint32_t *alias)
+{
+    size_t N = (size_t)1 << t->bits;
+    if (sym) memcpy(sym, t->sym, N * sizeof(uint64_t));
+    if (len) memcpy(len, t->len, N * sizeof(uint8_t));
+    if (p) memcpy(p, t->p, N * sizeof(double));
+    if (w) memcpy(w, t->w, N * sizeof(uint64_t));
+    if (thr) memcpy(thr, t->thr, N * sizeof(uint32_t));
+    if (alias) memcpy(alias, t->alias, N * sizeof(uint32_t));
+}
+
+/* Reading R7: column j = top b bits of the word, residual r = the other bits;
+ * the column's own entry if r < thr[j], else its alias. */
+uint32_t orc_draw(const orc_table *t, uint32_t u)
+{
+    uint32_t j = t->bits == 32 ? u : (u >> (32 - t->bits));
+    uint32_t r = u & (uint32_t)((((uint64_t)1) << (32 - t->bits)) - 1);
+    return r < t->thr[j] ? j : t->alias[j];
+}
+
+/* ------------------------------------------------------------------ */
+/* Sampling loop (Sec. 2 sampling-loop fragment, with reading R8)      */
+/* ------------------------------------------------------------------ */
+int orc_generate(const orc_table *const *tables, int ngroups, int k, int undirected,
+                 uint64_t seed, uint64_t e0, uint64_t count, uint64_t *row, uint64_t *col)
+{
+    if (ngroups < 1 || k < 1 || k > 64) return -1;
+    if (ngroups > 1) {
+        int sum = 0;
+        for (int g = 0; g < ngroups; ++g) sum += tables[g]->max_len;
+        if (sum != k) return -1;
+    }
+    for (uint64_t i = 0; i < count; ++i) {
+        uint64_t e = e0 + i;
+        uint64_t r = 0, c = 0;
+        int filled = 0;
+        uint64_t n = 0;
+        while (filled < k) {
+            const orc_table *t = tables[ngroups > 1 ? n : 0];
+            uint32_t u = orc_word(seed, e, n);
+            n++;
+            uint32_t sel = orc_draw(t, u);
+            int L = t->len[sel];
+            int take = L < k - filled ? L : k - filled;
+            for (int lvl = 0; lvl < take; ++lvl) {
+                int s = symbol_at(t->sym[sel], lvl);
+                r = (r << 1) | (uint64_t)(s >> 1);
+                c = (c << 1) | (uint64_t)(s & 1);
+            }
+            filled += take;
+        }
+        if (undirected && r > c) { uint64_t tmp = r; r = c; c = tmp; }
+        row[i] = r;
+        col[i] = c;
+    }
+    return 0;
+}
+
+/* Threshold round(x 2^32), saturated to 2^32 - 1. */
+static uint32_t naive_threshold(double x)
+{
+    double v = floor(ldexp(x, 32) + 0.5);
+    if (v >= 4294967295.0) return 0xFFFFFFFFu;
+    if (v <= 0.0) return 0;
+    return (uint32_t)v;
+}
+
+int orc_generate_naive(const double *Pin, int k, int undirected, uint64_t seed,
+                       uint64_t e0, uint64_t count, uint64_t *row, uint64_t *col)
+{
+    if (k < 1 || k > 64) return -1;
+    uint32_t *T = (uint32_t *)malloc((size_t)k * 3 * sizeof(uint32_t));
+    if (!T) return -1;
+    for (int lvl = 0; lvl < k; ++lvl) {
+        double P[4];
+        if (normalise(Pin + 4 * lvl, P) != 0) { free(T); return -1; }
+        T[3 * lvl + 0] = naive_threshold(P[0]);
+        T[3 * lvl + 1] = naive_threshold(P[0] + P[1]);
+        T[3 * lvl + 2] = naive_threshold((P[0] + P[1]) + P[2]);
+    }
+    for (uint64_t i = 0; i < count; ++i) {
+        uint64_t e = e0 + i;
+        uint64_t r = 0, c = 0;
+        for (int lvl = 0; lvl < k; ++lvl) {
+            uint32_t u = orc_word(seed, e, (uint64_t)lvl);
+            int s = (u >= T[3 * lvl]) + (u >= T[3 * lvl + 1]) + (u >= T[3 * lvl + 2]);
+            r = (r << 1) | (uint64_t)(s >> 1);
+            c = (c << 1) | (uint64_t)(s & 1);
+        }
+        if (undirected && r > c) { uint64_t tmp = r; r = c; c = tmp; }
+        row[i] = r;
+        col[i] = c;
+    }
+    free(T);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Exact edge distribution by enumeration of draw sequences            */
+/* ------------------------------------------------------------------ */
+static void dist_rec(const orc_table *const *tables, int ngroups, int k, int quantised,
+                     int draw, int filled, uint64_t r, uint64_t c, double prob, double *out)
+{
+    if (filled >= k) {
+        out[(r << k) | c] += prob;
+        return;
+    }
+    const orc_table *t = tables[ngroups > 1 ? draw : 0];
+    int N = 1 << t->bits;
+    for (int i = 0; i < N; ++i) {
+        double pi = quantised ? ldexp((double)t->w[i], -32) : t->p[i];
+        if (pi == 0.0) continue;
+        int L = t->len[i];
+        int take = L < k - filled ? L : k - filled;
+        uint64_t rr = r, cc = c;
+        for (int lvl = 0; lvl < take; ++lvl) {
+            int s = symbol_at(t->sym[i], lvl);
+            rr = (rr << 1) | (uint64_t)(s >> 1);
+            cc = (cc << 1) | (uint64_t)(s & 1);
+        }
+        dist_rec(tables, ngroups, k, quantised, draw + 1, filled + take, rr, cc, prob * pi, out);
+    }
+}
+
+int orc_edge_distribution(const orc_table *const *tables, int ngroups, int k,
+                          int quantised, double *out)
+{
+    if (k < 1 || k > 12 || ngroups < 1) return -1;
+    memset(out, 0, sizeof(double) * ((size_t)1 << (2 * k)));
+    dist_rec(tables, ngroups, k, quantised, 0, 0, 0, 0, 1.0, out);
+    return 0;
+}

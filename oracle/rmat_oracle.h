@@ -1,0 +1,90 @@
+/*
+ * rmat_oracle.h -- plain, slow, scalar CPU oracle for the alias-path R-MAT
+ * generator of Huebschle-Schneider & Sanders, "Linear Work Generation of R-MAT
+ * Graphs" (arXiv 1905.03525).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link or
+ * call this code: only the tests, the smoke check and the benchmark's CPU
+ * baseline leg use it.  It shares no code with the CUDA library.
+ *
+ * What it computes (paper section in brackets):
+ *   - path probabilities of the R-MAT recursion, FP64 products      [Sec. 1, Sec. 2]
+ *   - the variable-length table of similar-probability paths        [Sec. 2, table-construction fragment]
+ *   - the fixed-length table of all 4^l paths                       [Sec. 2]
+ *   - u32 quantisation + integer Walker/Vose alias table            [Sec. 2, Walker's alias method]
+ *   - Philox4x32-10 word stream keyed by (seed, edge index)         [Salmon et al., SC'11]
+ *   - the sampling loop: draw, concatenate path bits, cut at k      [Sec. 2, sampling-loop fragment]
+ *   - undirected mirroring (min, max)                               [Sec. 3]
+ *   - the naive per-bit R-MAT process (k quadrant draws per edge)   [Sec. 1]
+ *   - exact edge distribution implied by a table, by enumeration    [Sec. 1 definition, for pins]
+ *
+ * Conventions: symbol s = 2*rowbit + colbit, a->0, b->1, c->2, d->3 (Sec. 1:
+ * a = upper-left, b = upper-right, c = lower-left, d = lower-right; the
+ * table-construction fragment appends (0,0),(0,1),(1,0),(1,1) for a,b,c,d).
+ * Level 0 is the top recursion level = most significant bit of row/column.
+ */
+#ifndef RMAT_ORACLE_H
+#define RMAT_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct orc_table orc_table;
+
+/* Philox4x32-10 block function (Salmon, Moraes, Dror, Shaw, SC'11). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Word n (n = 0, 1, 2, ...) of the random stream of edge e under `seed`:
+ * key = (seed lo, seed hi), counter = (q lo, q hi, e lo, e hi), q = n / 4,
+ * and the word is output word n % 4 of that block. */
+uint32_t orc_word(uint64_t seed, uint64_t e, uint64_t n);
+
+/* Variable-length table (Sec. 2 table-construction fragment): repeated
+ * expansion of the maximum-probability entry while |Q| + 3 < bound.
+ * Depth cap min(k, 32).  NULL on invalid arguments. */
+orc_table *orc_table_variable(double a, double b, double c, double d, int k, uint64_t bound);
+
+/* Fixed-length table: all 4^ell paths of length ell, level t of a path using
+ * the parameters P[4*t .. 4*t+3].  NULL on invalid arguments. */
+orc_table *orc_table_fixed(const double *P, int ell);
+
+void orc_table_free(orc_table *t);
+
+int orc_table_entries(const orc_table *t); /* |Q| before padding */
+int orc_table_bits(const orc_table *t);    /* b: padded size N = 2^b */
+int orc_table_max_len(const orc_table *t);
+
+/* Copy out the table, each array of length N = 2^b (padding entries at the
+ * end have p = 0, len = 0).  sym: symbol string, 2 bits per level, first level
+ * in the top bits of the 64-bit word.  Any pointer may be NULL. */
+void orc_table_get(const orc_table *t, uint64_t *sym, uint8_t *len, double *p,
+                   uint64_t *w, uint32_t *thr, uint32_t *alias);
+
+/* One alias draw from 32-bit word u: index of the selected entry. */
+uint32_t orc_draw(const orc_table *t, uint32_t u);
+
+/* Generate edges e0 .. e0+count-1.  With ngroups == 1 every draw uses
+ * tables[0]; with ngroups > 1 draw g uses tables[g] and the groups' lengths
+ * must add up to k.  Returns 0, or -1 on invalid arguments. */
+int orc_generate(const orc_table *const *tables, int ngroups, int k, int undirected,
+                 uint64_t seed, uint64_t e0, uint64_t count, uint64_t *row, uint64_t *col);
+
+/* Naive per-bit R-MAT (Sec. 1): level t draws one quadrant from word t with
+ * thresholds round(a 2^32), round((a+b) 2^32), round((a+b+c) 2^32) of the
+ * level's normalised parameters P[4t..4t+3]. */
+int orc_generate_naive(const double *P, int k, int undirected, uint64_t seed,
+                       uint64_t e0, uint64_t count, uint64_t *row, uint64_t *col);
+
+/* Exact probability of every edge (row, col), out[row * 2^k + col], implied by
+ * drawing from the tables as orc_generate does.  quantised = 0 uses the FP64
+ * path probabilities p, quantised = 1 uses w / 2^32.  Intended for k <= 8. */
+int orc_edge_distribution(const orc_table *const *tables, int ngroups, int k,
+                          int quantised, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

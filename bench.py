@@ -1,0 +1,297 @@
+#!/usr/bin/env python3
+"""Benchmark: R-MAT edges/s on GB300 and the fraction of the HBM-write roofline.
+
+Default workload (one step = one pass of the whole sampling path over one
+graph): k = 26 (n = 2^26), m = 2^30 edges (edge factor 16), Graph 500
+parameters a, b, c, d = 0.57, 0.19, 0.19, 0.05, variable-length table with
+bound 2^12 (4093 entries), Philox seed 1, uint32 (row, col) pairs -- 8 GiB of
+output per step, far larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torchrun, one rank per GPU) every rank generates its
+own 2^30-edge range of one 2^30*N-edge graph (weak scaling; ranges are
+independent, no collective on the data path).  `--impl reference` times the
+CPU oracle on the host cores instead (bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+K, LOG2M, BOUND, SEED = 26, 30, 4096, 1
+G500 = (0.57, 0.19, 0.19, 0.05)
+METRIC = "R-MAT edges/s on 1 GB300, % of HBM-write roofline; batched vs per-graph launches"
+WORKLOAD = ("R-MAT k=26 (n=2^26), m=2^30 edges (edge factor 16), a,b,c,d=0.57,0.19,0.19,0.05, "
+            "variable-length similar-probability paths, table bound 2^12 (4093 entries), "
+            "Philox4x32-10 seed=1, u32 (row,col) pairs")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample-edges", type=int, default=1 << 27)
+    return ap.parse_args()
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self._t.join(timeout=2)
+
+    def summary(self):
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                maxs.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs), "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def cpu_baseline(total_edges: int):
+    """The oracle, as it stands, over a bounded sample of the workload on all
+    host cores (one thread per core, each generating consecutive edge ranges)."""
+    import numpy as np
+    import oracle
+    cores = os.cpu_count() or 1
+    t = oracle.Table.variable(*G500, K, BOUND)
+    per = (total_edges + cores - 1) // cores
+    chunk = 1 << 20
+
+    def work(c):
+        lo = c * per
+        hi = min(total_edges, lo + per)
+        L = oracle.lib()
+        row = np.zeros(chunk, np.uint64)
+        col = np.zeros(chunk, np.uint64)
+        h = oracle._handles([t])
+        e = lo
+        while e < hi:
+            n = min(chunk, hi - e)
+            L.orc_generate(h, 1, K, 0, SEED, e, n, row.ctypes.data, col.ctypes.data)
+            e += n
+
+    threads = [threading.Thread(target=work, args=(c,)) for c in range(cores)]
+    t0 = time.perf_counter()
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    dt = time.perf_counter() - t0
+    return {"value": total_edges / dt, "unit": "edges/s", "cores": cores, "kind": "oracle",
+            "sample": f"edges 0..{total_edges - 1} of the same graph (k=26, bound 2^12, seed 1), "
+                      f"{cores} threads, {dt:.1f} s wall"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n = args.cpu_sample_edges
+    vals = []
+    for _ in range(max(0, args.warmup)):
+        cpu_baseline(n // 8)
+    for _ in range(max(1, args.steps)):
+        vals.append(cpu_baseline(n // max(1, args.steps)))
+    v = statistics.median([x["value"] for x in vals])
+    cb = dict(vals[-1])
+    cb["value"] = v
+    cb["sample"] = f"{args.steps} steps of {n // max(1, args.steps)} edges each: " + cb["sample"]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "edges/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "k": K, "m": 1 << LOG2M, "table_bound": BOUND},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "edges/s", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import paper_1905_03525_gb300 as rm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    m = 1 << LOG2M
+    e0 = rank * m
+    table = rm.rmat_build_table(*G500, K, BOUND)
+    rm.rmat_table_upload(table)
+    out = rm.empty_edges(m, K)
+    stream = torch.cuda.Stream()
+
+    for _ in range(max(3, args.warmup)):
+        rm.rmat_generate(table, SEED, e0, m, out, stream)
+    stream.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t_begin = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_begin.record(stream)
+        for i in range(args.steps):
+            starts[i].record(stream)
+            rm.rmat_generate(table, SEED, e0, m, out, stream)
+            ends[i].record(stream)
+        t_end.record(stream)
+        stream.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    total_ms = t_begin.elapsed_time(t_end)
+    per_launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * m * args.steps / (total_ms / 1e3)
+
+    # roofline of the (only) kernel: algorithmic bytes = 8 B per edge written
+    peak, peak_src = measured_peak()
+    avg_launch_s = statistics.mean(per_launch_ms) / 1e3
+    achieved = 8.0 * m / avg_launch_s / 1e9
+    rm.rmat_check_device_errors()
+
+    # end to end through the public host-buffer call: table built and uploaded
+    # every step (h2d), all edges copied back into pinned host memory (d2h).
+    e2e = None
+    if not args.no_e2e:
+        host = rm.empty_edges(m, K, device="cpu", pin_memory=True)
+        img_bytes = rm.rmat_table_info(table)["device_image_bytes"]
+        rm.rmat_generate_host(table, SEED, e0, m, host, stream)  # warm the staging area
+        barrier()
+        times = []
+        for _ in range(max(1, min(args.steps, 3))):
+            t0 = time.perf_counter()
+            tb = rm.rmat_build_table(*G500, K, BOUND)
+            rm.rmat_table_upload(tb)
+            rm.rmat_generate_host(tb, SEED, e0, m, host, stream)
+            times.append(time.perf_counter() - t0)
+            tb.free()
+        tt = torch.tensor([statistics.median(times)], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * m / float(tt.item()), "unit": "edges/s", "h2d_bytes_per_step": int(img_bytes),
+               "d2h_bytes_per_step": int(8 * m), "steps": len(times),
+               "path": "rmat_build_table + rmat_table_upload + rmat_generate_host into pinned host memory"}
+        del host
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cb = None
+    if world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(args.cpu_sample_edges)
+    cs = clocks.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "k": K, "m_per_gpu": m, "table_bound": BOUND, "seed": SEED,
+                   "l2": "no flush: each step writes 8 GiB, far larger than the 126 MiB L2",
+                   "parallelism": f"edge-range sharding x{world}, no collective"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_source": f"{peak_src} hbm_gbs (copy)",
+                     "algorithmic_bytes_per_launch": 8 * m, "avg_launch_ms": avg_launch_s * 1e3},
+        "cpu_baseline": cb,
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": {"sm_mhz": cs["sm_mhz"], "sm_max_mhz": cs["sm_max_mhz"], "reasons": cs["reasons"]},
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

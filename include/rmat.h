@@ -1,0 +1,207 @@
+/*
+ * rmat.h -- C ABI of librmat, a GB300 (sm_103a) generator of R-MAT graphs with
+ * constant work per edge, after Huebschle-Schneider & Sanders, "Linear Work
+ * Generation of R-MAT Graphs" (arXiv 1905.03525).
+ *
+ * The R-MAT model (Sec. 1): a directed multigraph on n = 2^k nodes with m
+ * edges; each edge descends k times into one of the four quadrants of the
+ * adjacency matrix, upper-left with probability a, upper-right b, lower-left c,
+ * lower-right d (a + b + c + d = 1), emitting one row bit and one column bit
+ * per level.  The generator samples whole paths of that recursion at once from
+ * an alias table (Sec. 2) and concatenates their bits until k levels are
+ * filled.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns an rmat_status; nothing aborts.  On failure
+ *     rmat_last_error() returns a message (thread-local, valid until the
+ *     thread's next librmat call).  Arguments are checked on the host before
+ *     anything is launched.
+ *   - "device pointer" means memory of the current CUDA device (cudaMalloc,
+ *     torch.cuda, ...).  Output buffers are owned by the caller.
+ *   - Edge layout: an array of (row, col) pairs, row first.  Tables with
+ *     k <= 32 write uint32 pairs (8 bytes per edge), tables with k > 32 write
+ *     uint64 pairs (16 bytes per edge).
+ *   - Determinism: edge i of a call is edge number edge_offset + i of the
+ *     graph (table, seed), and its bytes depend only on (table, seed,
+ *     edge_offset + i): never on how a graph is split into calls, on the
+ *     launch shape, on batching or on serving.
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key = seed
+ *     and counter = (block q, edge index e); edge e consumes words 0, 1, 2,
+ *     ... of its own stream, one 32-bit word per alias draw.
+ */
+#ifndef RMAT_H
+#define RMAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *rmat_stream_t; /* same type as cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    RMAT_OK = 0,
+    RMAT_ERR_INVALID_ARGUMENT = 1, /* a parameter is out of range; nothing was launched */
+    RMAT_ERR_OUT_OF_MEMORY = 2,    /* a device or host allocation failed */
+    RMAT_ERR_CUDA = 3,             /* a CUDA runtime call failed (message has the CUDA error) */
+    RMAT_ERR_TIMEOUT = 4,          /* a bounded wait ran out (device flag or host deadline) */
+    RMAT_ERR_UNSUPPORTED = 5       /* no device, wrong architecture, or a table too large */
+} rmat_status;
+
+typedef struct rmat_table rmat_table; /* opaque; owned by the library */
+
+/* Table flags. */
+#define RMAT_UNDIRECTED 1u /* emit (min(r,c), max(r,c)): mirror the lower-left triangle (Sec. 3) */
+
+/*
+ * rmat_build_table -- variable-length table of similar-probability paths
+ * (Sec. 2, table-construction fragment).
+ *
+ * Starting from the empty path, the most probable entry is repeatedly replaced
+ * by its four children (probabilities ap, bp, cp, dp; bits (0,0), (0,1),
+ * (1,0), (1,1) appended to (row, col)) while |Q| + 3 < table_bound, which
+ * gives the largest table of 1 + 3t entries below the bound (Fig. 1 sizes:
+ * bound 2^12 -> 4093).  Ties go to the lexicographically smaller path; paths
+ * stop growing at min(k, 32) levels.  Path probabilities are FP64 products,
+ * quantised to u32 weights that sum to 2^32 (floor, then +1 to the largest
+ * fractional parts) and turned into an integer Vose alias table.
+ *
+ * a, b, c, d : quadrant probabilities, each >= 0, |a+b+c+d - 1| <= 1e-9; they
+ *              are divided by their sum before use.
+ * k          : levels = log2(nodes), 1 <= k <= 64.
+ * table_bound: 5 <= table_bound <= 2^24.
+ * out        : receives the new table (host memory; device copy made lazily).
+ */
+rmat_status rmat_build_table(double a, double b, double c, double d, int k,
+                             uint64_t table_bound, rmat_table **out);
+
+/*
+ * rmat_build_table_fixed -- all 4^ell paths of length ell (Sec. 2, "paths of a
+ * fixed length"), 1 <= ell <= 12.  Entry i is the path whose symbols are the
+ * base-4 digits of i (most significant digit = top level).  Same
+ * quantisation and alias construction as rmat_build_table.
+ */
+rmat_status rmat_build_table_fixed(double a, double b, double c, double d, int k, int ell,
+                                   rmat_table **out);
+
+/*
+ * rmat_build_table_levels -- per-level parameters, one fixed-length table per
+ * group of ell consecutive levels (Sec. 3, smoothing by perturbed parameters,
+ * in its exact form for noise shared by all edges).
+ *
+ * abcd : k x 4 doubles, row t = (a, b, c, d) of level t (level 0 = top = most
+ *        significant bit).  Each row is checked and normalised like above.
+ * ell  : group length, 1 <= ell <= 12; group g covers levels g*ell ..
+ *        min(k, (g+1)*ell) - 1 and is sampled with word g of the edge's stream.
+ * flags: RMAT_UNDIRECTED or 0.
+ * At most 64 groups.
+ */
+rmat_status rmat_build_table_levels(const double *abcd, int k, int ell, unsigned flags,
+                                    rmat_table **out);
+
+/* Set or clear flags (RMAT_UNDIRECTED) on an existing table. */
+rmat_status rmat_table_set_flags(rmat_table *t, unsigned flags);
+
+typedef struct {
+    int k;              /* levels */
+    int groups;         /* 1, or the number of level groups */
+    int entries;        /* |Q| of group 0 (before padding) */
+    int bits;           /* b of group 0: padded size 2^b */
+    int max_len;        /* longest path of any group, in levels */
+    int index_bytes;    /* 4 (k <= 32) or 8 */
+    unsigned flags;
+    uint64_t device_image_bytes; /* size of the device copy of all groups */
+} rmat_table_info_t;
+
+rmat_status rmat_table_info(const rmat_table *t, rmat_table_info_t *info);
+
+/* Entries and padded size of one group. */
+rmat_status rmat_table_group_info(const rmat_table *t, int group, int *entries, int *bits,
+                                  int *max_len);
+
+/*
+ * rmat_table_export -- copy out group `group` in canonical order (paths in
+ * lexicographic order, zero-probability padding at the end), arrays of length
+ * 2^bits.  sym: the path, 2 bits per level (2*rowbit + colbit), top level in
+ * bits 63..62; len: levels; p: FP64 probability; w: u32 weight (held in a
+ * uint64); thr/alias: the alias table (draw: column j = top `bits` bits of a
+ * word, residual r = the rest; entry j if r < thr[j], else alias[j]).
+ * Any pointer may be NULL.  Host memory.
+ */
+rmat_status rmat_table_export(const rmat_table *t, int group, uint64_t *sym, uint8_t *len,
+                              double *p, uint64_t *w, uint32_t *thr, uint32_t *alias);
+
+/* Upload the device copy now for the current device (otherwise the first
+ * rmat_generate on a device does it, synchronously).  Do this before
+ * capturing rmat_generate into a CUDA graph. */
+rmat_status rmat_table_upload(rmat_table *t);
+
+void rmat_free_table(rmat_table *t);
+
+/*
+ * rmat_generate -- edges edge_offset .. edge_offset+count-1 of the graph
+ * (table, seed) into `out` (device pointer, 8-byte aligned; 16-byte aligned
+ * lets the kernel use bulk (TMA) stores), count * 8 or 16 bytes.
+ * Asynchronous on `stream`; the caller synchronises.  count == 0 is a no-op.
+ * Sampling loop of Sec. 2: per edge, draw a path from the alias table with one
+ * Philox word, append its row/column bits, repeat until k levels are filled;
+ * the surplus levels of the last path are dropped (each edge has its own
+ * random stream, so no bits carry over between edges).
+ */
+rmat_status rmat_generate(const rmat_table *t, uint64_t seed, uint64_t edge_offset,
+                          uint64_t count, void *out, rmat_stream_t stream);
+
+/*
+ * rmat_generate_host -- as rmat_generate, but `host_out` is host memory
+ * (pinned memory gives full copy bandwidth).  Generates in device chunks and
+ * overlaps each chunk's device-to-host copy with the next chunk's
+ * generation.  Blocking: returns when all edges are in host_out.  Uses a
+ * library-owned device staging area (allocated on first use, kept).
+ */
+rmat_status rmat_generate_host(const rmat_table *t, uint64_t seed, uint64_t edge_offset,
+                               uint64_t count, void *host_out, rmat_stream_t stream);
+
+/*
+ * rmat_generate_naive -- the plain R-MAT process of Sec. 1: k quadrant draws
+ * per edge, level t using word t of the same Philox stream and the
+ * thresholds round(a 2^32), round((a+b) 2^32), round((a+b+c) 2^32) of level
+ * t's normalised parameters abcd[4t..4t+3].  Baseline only: same distribution
+ * as rmat_generate, not the same bits.  Output layout as rmat_generate.
+ */
+rmat_status rmat_generate_naive(const double *abcd, int k, unsigned flags, uint64_t seed,
+                                uint64_t edge_offset, uint64_t count, void *out,
+                                rmat_stream_t stream);
+
+/*
+ * Launch shape.  rmat_generate uses the autotuned shape for (table, device)
+ * when one was recorded with rmat_set_launch_config, else a default.
+ * threads: 128..1024, multiple of 32; ctas_per_sm: 1..8; tile_edges: edges
+ * per warp tile, multiple of 32, 32..1024.  Results never depend on it.
+ */
+typedef struct {
+    int threads;
+    int ctas_per_sm;
+    int tile_edges;
+} rmat_launch_config_t;
+
+rmat_status rmat_set_launch_config(rmat_table *t, const rmat_launch_config_t *cfg);
+rmat_status rmat_get_launch_config(const rmat_table *t, rmat_launch_config_t *cfg);
+
+/* ---------------------------------------------------------------------- */
+/* Device error flag                                                       */
+/* ---------------------------------------------------------------------- */
+/* Read and clear the device-side error flag (non-zero when a kernel's
+ * bounded wait gave up).  Synchronises the device.  RMAT_ERR_TIMEOUT if set. */
+rmat_status rmat_check_device_errors(void);
+
+/* Library version string and the compiled GPU architecture. */
+const char *rmat_version(void);
+
+const char *rmat_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,185 @@
+"""GB300-native R-MAT generation with constant work per edge (arXiv 1905.03525).
+
+Python binding of librmat with the same names as the C ABI in include/rmat.h.
+Tables are built on the host by the library; every edge is generated by the
+library's sm_103a kernels.  PyTorch, when used, only supplies device memory
+and streams: ``out`` arguments accept a CUDA tensor or a raw device address,
+``stream`` accepts a ``torch.cuda.Stream``, a raw handle or None.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from ._capi import (RMAT_UNDIRECTED, LaunchConfig, RmatError, TableInfo, check, lib)
+
+__all__ = [
+    "RMAT_UNDIRECTED", "RmatError", "Table", "rmat_build_table", "rmat_build_table_fixed",
+    "rmat_build_table_levels", "rmat_table_set_flags", "rmat_table_info", "rmat_table_group_info",
+    "rmat_table_export", "rmat_table_upload", "rmat_free_table", "rmat_generate", "rmat_generate_host",
+    "rmat_generate_naive", "rmat_set_launch_config", "rmat_get_launch_config",
+    "rmat_check_device_errors", "rmat_version", "edge_bytes", "empty_edges",
+]
+
+
+class Table:
+    """Owning handle of an ``rmat_table``; freed with the object."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("table already freed")
+        return self._h
+
+    def free(self):
+        if self._h:
+            lib().rmat_free_table(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    @property
+    def info(self) -> dict:
+        return rmat_table_info(self)
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return int(x.ctypes.data)
+    raise TypeError(f"cannot take an address of {type(x)!r}")
+
+
+def _stream(s) -> int:
+    if s is None:
+        return 0
+    if isinstance(s, int):
+        return s
+    if hasattr(s, "cuda_stream"):
+        return int(s.cuda_stream)
+    raise TypeError(f"not a stream: {type(s)!r}")
+
+
+def _new_table(call) -> Table:
+    h = ctypes.c_void_p()
+    check(call(ctypes.byref(h)))
+    return Table(h)
+
+
+def rmat_build_table(a, b, c, d, k, table_bound) -> Table:
+    """Variable-length table of similar-probability paths (Sec. 2)."""
+    return _new_table(lambda out: lib().rmat_build_table(a, b, c, d, k, table_bound, out))
+
+
+def rmat_build_table_fixed(a, b, c, d, k, ell) -> Table:
+    """All 4^ell paths of length ell (Sec. 2)."""
+    return _new_table(lambda out: lib().rmat_build_table_fixed(a, b, c, d, k, ell, out))
+
+
+def rmat_build_table_levels(abcd, k, ell, flags=0) -> Table:
+    """Per-level parameters (k x 4), one fixed-length table per ell levels (Sec. 3)."""
+    P = np.ascontiguousarray(abcd, dtype=np.float64).reshape(-1, 4)
+    if P.shape[0] != k:
+        raise ValueError("abcd must have k rows")
+    return _new_table(lambda out: lib().rmat_build_table_levels(P.ctypes.data, k, ell, flags, out))
+
+
+def rmat_table_set_flags(t: Table, flags: int) -> None:
+    check(lib().rmat_table_set_flags(t.handle, flags))
+
+
+def rmat_table_info(t: Table) -> dict:
+    info = TableInfo()
+    check(lib().rmat_table_info(t.handle, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in TableInfo._fields_}
+
+
+def rmat_table_group_info(t: Table, group: int):
+    e, b, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    check(lib().rmat_table_group_info(t.handle, group, ctypes.byref(e), ctypes.byref(b), ctypes.byref(m)))
+    return e.value, b.value, m.value
+
+
+def rmat_table_export(t: Table, group: int = 0) -> dict:
+    entries, bits, max_len = rmat_table_group_info(t, group)
+    N = 1 << bits
+    out = {"sym": np.zeros(N, np.uint64), "len": np.zeros(N, np.uint8), "p": np.zeros(N, np.float64),
+           "w": np.zeros(N, np.uint64), "thr": np.zeros(N, np.uint32), "alias": np.zeros(N, np.uint32)}
+    check(lib().rmat_table_export(t.handle, group, *[out[x].ctypes.data for x in
+                                                     ("sym", "len", "p", "w", "thr", "alias")]))
+    out.update(entries=entries, bits=bits, max_len=max_len)
+    return out
+
+
+def rmat_table_upload(t: Table) -> None:
+    check(lib().rmat_table_upload(t.handle))
+
+
+def rmat_free_table(t: Table) -> None:
+    t.free()
+
+
+def edge_bytes(k: int) -> int:
+    """Bytes per edge of the output layout: uint32 pairs for k <= 32, else uint64."""
+    return 8 if k <= 32 else 16
+
+
+def empty_edges(count: int, k: int, device="cuda", pin_memory=False):
+    """Allocate an output buffer for `count` edges as a torch tensor of shape
+    (count, 2), uint32 (k <= 32) or int64 holding uint64 bits (k > 32)."""
+    import torch
+    dt = torch.int32 if k <= 32 else torch.int64
+    if device == "cpu":
+        return torch.empty((count, 2), dtype=dt, pin_memory=pin_memory)
+    return torch.empty((count, 2), dtype=dt, device=device)
+
+
+def rmat_generate(t: Table, seed: int, edge_offset: int, count: int, out, stream=None) -> None:
+    """Edges edge_offset .. edge_offset+count-1 into device memory `out` (async)."""
+    check(lib().rmat_generate(t.handle, seed, edge_offset, count, _ptr(out), _stream(stream)))
+
+
+def rmat_generate_host(t: Table, seed: int, edge_offset: int, count: int, host_out, stream=None) -> None:
+    """Edges into host memory (blocking; pinned memory gives full bandwidth)."""
+    check(lib().rmat_generate_host(t.handle, seed, edge_offset, count, _ptr(host_out), _stream(stream)))
+
+
+def rmat_generate_naive(abcd, k, flags, seed, edge_offset, count, out, stream=None) -> None:
+    """Plain per-bit R-MAT (Sec. 1) on the GPU: k quadrant draws per edge."""
+    P = np.ascontiguousarray(abcd, dtype=np.float64).reshape(-1, 4)
+    if P.shape[0] == 1:
+        P = np.repeat(P, k, axis=0)
+    check(lib().rmat_generate_naive(P.ctypes.data, k, flags, seed, edge_offset, count, _ptr(out),
+                                    _stream(stream)))
+
+
+def rmat_set_launch_config(t: Table, threads: int, ctas_per_sm: int, tile_edges: int) -> None:
+    cfg = LaunchConfig(threads, ctas_per_sm, tile_edges)
+    check(lib().rmat_set_launch_config(t.handle, ctypes.byref(cfg)))
+
+
+def rmat_get_launch_config(t: Table) -> dict:
+    cfg = LaunchConfig()
+    check(lib().rmat_get_launch_config(t.handle, ctypes.byref(cfg)))
+    return {"threads": cfg.threads, "ctas_per_sm": cfg.ctas_per_sm, "tile_edges": cfg.tile_edges}
+
+
+def rmat_check_device_errors() -> None:
+    check(lib().rmat_check_device_errors())
+
+
+def rmat_version() -> str:
+    return lib().rmat_version().decode()

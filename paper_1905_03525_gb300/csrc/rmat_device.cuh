@@ -1,0 +1,200 @@
+// rmat_device.cuh -- device building blocks of the sampling kernels (sm_103a):
+// Philox4x32-10, the alias draw, path concatenation, and the TMA / mbarrier
+// primitives (inline PTX) used to stage tables and store edge tiles.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rmat {
+namespace dev {
+
+// --------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Counter (c0..c3) =
+// (block q lo, q hi, edge lo, edge hi), key = (seed lo, seed hi).  Each round
+// multiplies the even counter words by the round constants (one 32x32->64
+// multiply each), xors the high halves with the odd words and the round key,
+// and keeps the low halves; the key advances by the Weyl constants.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t m0 = uint64_t(0xD2511F53u) * c0;
+        const uint64_t m1 = uint64_t(0xCD9E8D57u) * c2;
+        const uint32_t n0 = uint32_t(m1 >> 32) ^ c1 ^ k0;
+        const uint32_t n2 = uint32_t(m0 >> 32) ^ c3 ^ k1;
+        c1 = uint32_t(m1);
+        c3 = uint32_t(m0);
+        c0 = n0;
+        c2 = n2;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// x >> n with n >= 32 giving 0 (one funnel shift).
+__device__ __forceinline__ uint32_t shr_clamp(uint32_t x, uint32_t n) {
+    return __funnelshift_rc(x, 0u, n);
+}
+
+template <bool SMEM>
+__device__ __forceinline__ uint32_t ld_word(const uint32_t *p) {
+    if constexpr (SMEM) return *p;
+    else return __ldg(p);
+}
+
+template <bool SMEM>
+__device__ __forceinline__ uint4 ld_quad(const uint32_t *p) {
+    if constexpr (SMEM) return *reinterpret_cast<const uint4 *>(p);
+    else return __ldg(reinterpret_cast<const uint4 *>(p));
+}
+
+// One alias draw from word u: column j = top `bits` bits, residual r = the
+// rest; keep j iff r < thr[j].  A[j] = (thr[j] << bits) | alias[j], and
+// ((u << bits) | mask) < A[j]  <=>  r < thr[j].
+template <bool SMEM>
+__device__ __forceinline__ uint32_t alias_select(const uint32_t *A, uint32_t u, uint32_t bits,
+                                                 uint32_t mask) {
+    const uint32_t j = u >> (32u - bits);
+    const uint32_t a = ld_word<SMEM>(A + j);
+    const uint32_t rs = (u << bits) | mask;
+    return rs < a ? j : (a & mask);
+}
+
+// Row bits (left-aligned in 32), column bits (left-aligned) and length of
+// entry `sel`.
+template <int FMT, bool SMEM>
+__device__ __forceinline__ void fetch_path(const uint32_t *B, uint32_t sel, uint32_t &r,
+                                           uint32_t &c, uint32_t &L) {
+    if constexpr (FMT == 0) {
+        const uint32_t p = ld_word<SMEM>(B + sel);
+        r = p & 0xFFF80000u;
+        c = p << 19;
+        L = (p >> 13) & 63u;
+    } else {
+        const uint4 v = ld_quad<SMEM>(B + 4 * sel);
+        r = v.x;
+        c = v.y;
+        L = v.z;
+    }
+}
+
+// Left-aligned accumulators.  Appending a path ORs its bits in below the
+// `filled` levels already present; bits that fall below the accumulator are
+// the surplus of the last path and are dropped.
+struct Acc32 {
+    uint32_t row, col, filled;
+    __device__ __forceinline__ void clear() { row = col = filled = 0; }
+    __device__ __forceinline__ void append(uint32_t r, uint32_t c, uint32_t L) {
+        row |= shr_clamp(r, filled);
+        col |= shr_clamp(c, filled);
+        filled += L;
+    }
+    __device__ __forceinline__ uint64_t out_row(int k) const { return row >> (32 - k); }
+    __device__ __forceinline__ uint64_t out_col(int k) const { return col >> (32 - k); }
+};
+
+struct Acc64 {
+    uint64_t row, col;
+    uint32_t filled;
+    __device__ __forceinline__ void clear() { row = col = 0; filled = 0; }
+    // Only called while filled < k <= 64.
+    __device__ __forceinline__ void append(uint32_t r, uint32_t c, uint32_t L) {
+        row |= (uint64_t(r) << 32) >> filled;
+        col |= (uint64_t(c) << 32) >> filled;
+        filled += L;
+    }
+    __device__ __forceinline__ uint64_t out_row(int k) const { return row >> (64 - k); }
+    __device__ __forceinline__ uint64_t out_col(int k) const { return col >> (64 - k); }
+};
+
+// --------------------------------------------------------------------------
+// PTX helpers: mbarrier, TMA bulk copies (global <-> shared), proxy fences.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: gives up after `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t it = 0; it < limit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (it > 16) __nanosleep(128);
+    }
+    return false;
+}
+
+// global -> shared bulk copy completing on an mbarrier (16-byte aligned
+// addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst_smem)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// shared -> global bulk copy in the thread's bulk async-group.
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src_smem, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+                 "r"(smem_u32(src_smem)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// Wait until at most one committed group is still reading shared memory.
+__device__ __forceinline__ void bulk_wait_read_1() {
+    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_all() {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// Make this thread's generic-proxy shared-memory writes visible to the async
+// (TMA) proxy.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t lane_mask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+}  // namespace dev
+}  // namespace rmat

@@ -1,0 +1,96 @@
+// rmat_internal.h -- internal types shared by the librmat translation units.
+#pragma once
+
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "rmat.h"
+
+namespace rmat {
+
+// One alias table: the canonical list of paths plus its alias structure
+// (one per level group for per-level tables).
+struct PathTable {
+    int entries = 0;               // |Q|
+    int bits = 0;                  // b, padded size N = 2^b
+    int max_len = 0;               // longest path (levels)
+    int min_len = 0;               // shortest path with non-zero weight
+    std::vector<uint64_t> sym;     // path symbols, top level in bits 63..62
+    std::vector<uint8_t> len;      // path length (levels)
+    std::vector<double> p;         // FP64 path probability
+    std::vector<uint64_t> w;       // u32 weight, sum 2^32
+    std::vector<uint32_t> thr;     // alias threshold, < 2^(32-b)
+    std::vector<uint32_t> alias;   // alias target
+};
+
+// Device table image formats (see rmat_image.cpp).
+enum ImageFormat : int {
+    kCompact = 0,  // paths <= 13 levels: A = (thr << b) | alias (u32), B = packed path (u32)
+    kWide = 1      // paths <= 32 levels: A as above, B = {row bits, col bits, len, 0} (uint4)
+};
+
+struct GroupDesc {
+    uint32_t a_off_words;  // offset of A in the image, in u32 words
+    uint32_t b_off_words;  // offset of B in the image, in u32 words
+    int bits;
+    int len;               // levels of this group (per-level tables)
+};
+
+struct DeviceCopy {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+// Launch shape of the sampling kernel for one table on one device.
+struct AliasPlan {
+    int fmt = 0;
+    bool u64 = false;
+    bool levels = false;
+    bool smem_table = true;
+    int threads = 0;
+    int tile = 0;
+    int ctas_per_sm = 0;
+    int sms = 0;
+    size_t smem_bytes = 0;
+    void *kernel = nullptr;
+    unsigned *err = nullptr;
+};
+
+}  // namespace rmat
+
+struct rmat_table {
+    int k = 0;
+    unsigned flags = 0;
+    bool per_level = false;                 // draw g uses group g
+    std::vector<rmat::PathTable> groups;
+    int format = rmat::kCompact;
+    std::vector<uint32_t> image;            // host copy of the device image
+    std::vector<rmat::GroupDesc> gdesc;
+    std::mutex mu;
+    std::map<int, rmat::DeviceCopy> dev;    // device ordinal -> copy
+    bool cfg_set = false;
+    rmat_launch_config_t cfg{};
+    std::map<int, rmat::AliasPlan> plans;   // device ordinal -> launch plan
+};
+
+namespace rmat {
+
+// Thread-local error message; returns `st` for convenient `return fail(...)`.
+rmat_status fail(rmat_status st, const std::string &msg);
+void clear_error();
+
+// Table construction (rmat_table.cpp).
+rmat_status build_variable(const double P[4], int k, uint64_t bound, PathTable &out);
+rmat_status build_fixed(const double *P_levels, int ell, PathTable &out);
+rmat_status normalise_params(const double in[4], double out[4]);
+
+// Device image (rmat_image.cpp): fills t->image / t->gdesc / t->format.
+rmat_status build_image(rmat_table *t);
+
+// Upload of the image for the current device (rmat_api.cu).
+rmat_status ensure_device_copy(const rmat_table *t, const uint32_t **dptr);
+
+}  // namespace rmat

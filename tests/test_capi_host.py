@@ -1,0 +1,142 @@
+"""Host-side checks of librmat that need no GPU: the library loads, exports
+every function that include/rmat.h declares, validates arguments, and builds
+tables identical (field by field) to the oracle's independent construction."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1905_03525_gb300 as rm
+from paper_1905_03525_gb300 import _capi, build as rm_build
+from paper_1905_03525_gb300.workloads import G500, SKEWED, noisy_levels
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ASYM = (0.5, 0.2, 0.25, 0.05)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    rm_build.build()
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(rmat_[A-Za-z0-9_]+)\s*\(",
+                             src, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("rmat_build_table", "rmat_generate", "rmat_free_table", "rmat_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = ctypes.CDLL(_capi.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+    bound = {name for name, _, _ in _capi.SIGNATURES}
+    assert set(declared_functions()) <= bound | {"rmat_no_alloc_placeholder"}
+
+
+def _compare(lib_export, ot):
+    N = 1 << ot.bits
+    assert lib_export["entries"] == ot.entries
+    assert lib_export["bits"] == ot.bits
+    assert lib_export["max_len"] == ot.max_len
+    for f in ("sym", "len", "p", "w", "thr", "alias"):
+        a, b = lib_export[f], getattr(ot, f)
+        assert a.shape == (N,)
+        assert np.array_equal(a, b), f
+
+
+@pytest.mark.parametrize("params,k,bound", [
+    (G500, 26, 4096), (G500, 16, 256), (ASYM, 20, 1000), (SKEWED, 30, 8192), (SKEWED, 64, 5000),
+    (G500, 4, 4096), (G500, 30, 5), (G500, 34, 1 << 16), ((0.25, 0.25, 0.25, 0.25), 20, 4096),
+    ((0.6, 0.2, 0.2, 0.0), 12, 777)])
+def test_variable_table_matches_oracle(params, k, bound):
+    t = rm.rmat_build_table(*params, k, bound)
+    _compare(rm.rmat_table_export(t), oracle.Table.variable(*params, k, bound))
+
+
+@pytest.mark.parametrize("params,ell", [(G500, 4), (ASYM, 1), (ASYM, 6), (SKEWED, 9), ((1.0, 0, 0, 0), 3)])
+def test_fixed_table_matches_oracle(params, ell):
+    t = rm.rmat_build_table_fixed(*params, 20, ell)
+    _compare(rm.rmat_table_export(t), oracle.Table.fixed([params], ell))
+
+
+@pytest.mark.parametrize("k,ell", [(34, 6), (34, 5), (7, 3), (12, 12), (64, 4)])
+def test_level_tables_match_oracle(k, ell):
+    P = noisy_levels(k, seed=k * 100 + ell)
+    t = rm.rmat_build_table_levels(P, k, ell)
+    groups = oracle.level_groups(P, k, ell)
+    info = rm.rmat_table_info(t)
+    assert info["groups"] == len(groups)
+    for g, ot in enumerate(groups):
+        _compare(rm.rmat_table_export(t, g), ot)
+
+
+def test_table_info():
+    t = rm.rmat_build_table(*G500, 26, 4096)
+    info = rm.rmat_table_info(t)
+    assert info["entries"] == 4093 and info["bits"] == 12 and info["index_bytes"] == 4
+    assert info["max_len"] == 13 and info["groups"] == 1
+    assert info["device_image_bytes"] == 4096 * 8
+    t64 = rm.rmat_build_table_levels(noisy_levels(34), 34, 6, rm.RMAT_UNDIRECTED)
+    i64 = rm.rmat_table_info(t64)
+    assert i64["index_bytes"] == 8 and i64["groups"] == 6 and i64["flags"] == 1
+
+
+@pytest.mark.parametrize("call", [
+    lambda: rm.rmat_build_table(0.5, 0.5, 0.5, 0.5, 10, 4096),
+    lambda: rm.rmat_build_table(*G500, 0, 4096),
+    lambda: rm.rmat_build_table(*G500, 65, 4096),
+    lambda: rm.rmat_build_table(*G500, 10, 4),
+    lambda: rm.rmat_build_table(*G500, 10, (1 << 24) + 1),
+    lambda: rm.rmat_build_table(float("nan"), 0.2, 0.2, 0.6, 10, 100),
+    lambda: rm.rmat_build_table(-0.1, 0.5, 0.5, 0.1, 10, 100),
+    lambda: rm.rmat_build_table_fixed(*G500, 10, 0),
+    lambda: rm.rmat_build_table_fixed(*G500, 10, 13),
+    lambda: rm.rmat_build_table_levels(np.tile(G500, (10, 1)), 10, 0),
+    lambda: rm.rmat_build_table_levels(np.tile(G500, (65, 1)), 65, 1),
+    lambda: rm.rmat_build_table_levels(np.tile(G500, (10, 1)), 10, 2, flags=8),
+])
+def test_invalid_arguments_are_rejected_on_host(call):
+    with pytest.raises(rm.RmatError) as ei:
+        call()
+    assert ei.value.status == _capi.RMAT_ERR_INVALID_ARGUMENT
+    assert ei.value.message
+
+
+def test_generate_argument_checks_need_no_device():
+    t = rm.rmat_build_table(*G500, 26, 4096)
+    with pytest.raises(rm.RmatError) as ei:
+        rm.rmat_generate(t, 1, 0, 10, 0)          # NULL output
+    assert ei.value.status == _capi.RMAT_ERR_INVALID_ARGUMENT
+    with pytest.raises(rm.RmatError) as ei:
+        rm.rmat_generate(t, 1, 0, 10, 0x1004)     # misaligned
+    assert ei.value.status == _capi.RMAT_ERR_INVALID_ARGUMENT
+    with pytest.raises(rm.RmatError) as ei:
+        rm.rmat_generate(t, 1, 2 ** 64 - 5, 10, 0x1000)  # index overflow
+    assert ei.value.status == _capi.RMAT_ERR_INVALID_ARGUMENT
+    rm.rmat_generate(t, 1, 0, 0, 0)               # count == 0 is a no-op
+
+
+def test_launch_config_roundtrip_and_checks():
+    t = rm.rmat_build_table(*G500, 26, 4096)
+    rm.rmat_set_launch_config(t, 256, 4, 128)
+    assert rm.rmat_get_launch_config(t) == {"threads": 256, "ctas_per_sm": 4, "tile_edges": 128}
+    with pytest.raises(rm.RmatError):
+        rm.rmat_set_launch_config(t, 100, 1, 128)
+    with pytest.raises(rm.RmatError):
+        rm.rmat_set_launch_config(t, 256, 1, 40)

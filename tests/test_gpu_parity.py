@@ -1,0 +1,228 @@
+"""GPU parity: librmat's kernels against the CPU oracle, bit for bit.
+
+Every case runs through the C ABI (the ctypes binding) on seeded synthetic
+inputs.  Small cases compare every edge; the full-size cases (the 2^30-edge
+k = 26 workload in the benchmark's launch shape, and one 2^30-edge chunk of
+the k = 34 per-level workload) compare sampled runs of edges that the oracle
+recomputes one by one, plus whole-output properties.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1905_03525_gb300 as rm
+from paper_1905_03525_gb300.workloads import G500, SKEWED, noisy_levels
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ASYM = (0.5, 0.2, 0.25, 0.05)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1905_03525_gb300 import build
+    build.build()
+    yield
+    torch.cuda.synchronize()
+    rm.rmat_check_device_errors()
+
+
+def as_u64_pairs(t, k):
+    """(count, 2) device tensor -> host (row, col) uint64 arrays."""
+    h = t.cpu().numpy()
+    if k <= 32:
+        h = h.view(np.uint32)
+    else:
+        h = h.view(np.uint64)
+    return h[:, 0].astype(np.uint64), h[:, 1].astype(np.uint64)
+
+
+def gpu_edges(table, k, seed, e0, count, stream=None):
+    out = rm.empty_edges(count, k)
+    rm.rmat_generate(table, seed, e0, count, out, stream)
+    torch.cuda.synchronize()
+    return as_u64_pairs(out, k)
+
+
+def assert_same(gpu, ref):
+    r_g, c_g = gpu
+    r_o, c_o = ref
+    bad = np.nonzero((r_g != r_o) | (c_g != c_o))[0]
+    assert bad.size == 0, f"{bad.size} edges differ; first at {bad[:5]}: gpu {r_g[bad[:3]]},{c_g[bad[:3]]} oracle {r_o[bad[:3]]},{c_o[bad[:3]]}"
+
+
+# ----------------------------------------------------------- whole outputs --
+
+def test_plain_k16_fixed_l4_full():
+    """k = 16, m = 2^20, Graph 500 parameters, fixed l = 4 (256 entries), seed 1."""
+    k, m = 16, 1 << 20
+    t = rm.rmat_build_table_fixed(*G500, k, 4)
+    assert_same(gpu_edges(t, k, 1, 0, m), oracle.generate([oracle.Table.fixed([G500], 4)], k, 1, 0, m))
+
+
+@pytest.mark.parametrize("count,e0", [(1, 0), (31, 7), (33, 0), (4097, 12345), ((1 << 18) + 37, (1 << 32) - 1000)])
+def test_k26_variable_ragged(count, e0):
+    k = 26
+    t = rm.rmat_build_table(*G500, k, 4096)
+    ot = oracle.Table.variable(*G500, k, 4096)
+    assert_same(gpu_edges(t, k, 1, e0, count), oracle.generate([ot], k, 1, e0, count))
+
+
+@pytest.mark.parametrize("params,k,bound", [
+    (G500, 26, 256), (ASYM, 20, 1000), (SKEWED, 26, 8192), (SKEWED, 32, 4096),
+    (G500, 1, 16), (G500, 32, 4096), (G500, 33, 4096), (SKEWED, 64, 4096), (G500, 40, 5),
+    (G500, 26, 1 << 16),   # table larger than shared memory: read from global
+    (SKEWED, 30, 1 << 15),  # paths > 13 levels (wide entries), global table
+])
+def test_variable_tables(params, k, bound):
+    m = 50_000
+    t = rm.rmat_build_table(*params, k, bound)
+    ot = oracle.Table.variable(*params, k, bound)
+    assert_same(gpu_edges(t, k, 99, 3, m), oracle.generate([ot], k, 99, 3, m))
+
+
+@pytest.mark.parametrize("params,k,ell", [(G500, 26, 6), (ASYM, 9, 4), (G500, 34, 5), (ASYM, 12, 12),
+                                          (SKEWED, 64, 7), (G500, 3, 5)])
+def test_fixed_tables(params, k, ell):
+    m = 40_000
+    t = rm.rmat_build_table_fixed(*params, k, ell)
+    assert_same(gpu_edges(t, k, 5, 0, m), oracle.generate([oracle.Table.fixed([params], ell)], k, 5, 0, m))
+
+
+@pytest.mark.parametrize("k,ell,undirected", [(34, 6, True), (34, 5, True), (34, 5, False), (20, 3, True),
+                                              (7, 12, False), (64, 4, True)])
+def test_per_level_tables(k, ell, undirected):
+    m = 40_000
+    P = noisy_levels(k, seed=7 + k + ell)
+    t = rm.rmat_build_table_levels(P, k, ell, rm.RMAT_UNDIRECTED if undirected else 0)
+    ref = oracle.generate(oracle.level_groups(P, k, ell), k, 34, 1 << 34, m, undirected=undirected)
+    assert_same(gpu_edges(t, k, 34, 1 << 34, m), ref)
+
+
+def test_undirected_flag_on_single_table():
+    k, m = 26, 20_000
+    t = rm.rmat_build_table(*G500, k, 4096)
+    rm.rmat_table_set_flags(t, rm.RMAT_UNDIRECTED)
+    ref = oracle.generate([oracle.Table.variable(*G500, k, 4096)], k, 3, 0, m, undirected=True)
+    assert_same(gpu_edges(t, k, 3, 0, m), ref)
+
+
+@pytest.mark.parametrize("params,k", [(G500, 26), (ASYM, 13), (G500, 40)])
+def test_naive_kernel_matches_oracle(params, k):
+    m = 30_000
+    out = rm.empty_edges(m, k)
+    rm.rmat_generate_naive(params, k, 0, 17, 100, m, out)
+    torch.cuda.synchronize()
+    assert_same(as_u64_pairs(out, k), oracle.generate_naive([params], k, 17, 100, m))
+
+
+def test_launch_shape_does_not_change_output():
+    k, m = 26, (1 << 17) + 5
+    t = rm.rmat_build_table(*G500, k, 4096)
+    ref = gpu_edges(t, k, 8, 0, m)
+    for threads, ctas, tile in [(128, 1, 32), (256, 4, 64), (512, 2, 1024), (1024, 1, 256), (1024, 1, 512)]:
+        rm.rmat_set_launch_config(t, threads, ctas, tile)
+        assert_same(gpu_edges(t, k, 8, 0, m), ref)
+
+
+def test_chunking_does_not_change_output():
+    k, m = 26, 100_000
+    t = rm.rmat_build_table(*G500, k, 4096)
+    whole = gpu_edges(t, k, 4, 0, m)
+    parts = [gpu_edges(t, k, 4, a, b - a) for a, b in [(0, 1), (1, 33333), (33333, 33334), (33334, m)]]
+    r = np.concatenate([p[0] for p in parts])
+    c = np.concatenate([p[1] for p in parts])
+    assert_same((r, c), whole)
+
+
+def test_unaligned_output_and_guard_region():
+    """An output that is 8- but not 16-byte aligned takes the plain-store path;
+    nothing outside [out, out + count) is written."""
+    k, m = 26, 10_001
+    t = rm.rmat_build_table(*G500, k, 4096)
+    buf = torch.full((m + 64, 2), -1, dtype=torch.int32, device="cuda")
+    view = buf[1:1 + m]
+    assert view.data_ptr() % 16 == 8
+    rm.rmat_generate(t, 6, 0, m, view)
+    torch.cuda.synchronize()
+    assert_same(as_u64_pairs(view, k), oracle.generate([oracle.Table.variable(*G500, k, 4096)], k, 6, 0, m))
+    h = buf.cpu()
+    assert bool((h[0] == -1).all()) and bool((h[1 + m:] == -1).all())
+
+
+def test_generate_host_matches_device():
+    k, m = 26, (1 << 26) + 11   # crosses the 256 MiB staging chunk
+    t = rm.rmat_build_table(*G500, k, 4096)
+    dev = rm.empty_edges(m, k)
+    rm.rmat_generate(t, 2, 5, m, dev)
+    host = rm.empty_edges(m, k, device="cpu", pin_memory=True)
+    rm.rmat_generate_host(t, 2, 5, m, host)
+    torch.cuda.synchronize()
+    assert torch.equal(dev.cpu(), host)
+
+
+def test_streams_are_honoured():
+    k, m = 26, 1 << 20
+    t = rm.rmat_build_table(*G500, k, 4096)
+    s = torch.cuda.Stream()
+    out = rm.empty_edges(m, k)
+    with torch.cuda.stream(s):
+        rm.rmat_generate(t, 1, 0, m, out, s)
+    s.synchronize()
+    assert_same(as_u64_pairs(out[:4096], k), oracle.generate([oracle.Table.variable(*G500, k, 4096)], k, 1, 0, 4096))
+
+
+# --------------------------------------------------------- full-size cases --
+
+def _sample_ranges(m, rng, n=24, width=2048):
+    starts = {0, m - width}
+    while len(starts) < n:
+        starts.add(int(rng.integers(0, m - width)))
+    return sorted(starts)
+
+
+def test_k26_full_size_in_bench_shape():
+    """k = 26, m = 2^30 (edge factor 16), variable table bound 2^12: the
+    benchmark's workload and launch shape.  Sampled edges are recomputed by the
+    oracle; whole-output marginals must match the Kronecker closed form."""
+    k, m = 26, 1 << 30
+    t = rm.rmat_build_table(*G500, k, 4096)
+    ot = oracle.Table.variable(*G500, k, 4096)
+    out = rm.empty_edges(m, k)
+    rm.rmat_generate(t, 1, 0, m, out)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(26)
+    for s in _sample_ranges(m, rng):
+        assert_same(as_u64_pairs(out[s:s + 2048], k), oracle.generate([ot], k, 1, s, 2048))
+    # property at full size: the top-level quadrant frequencies
+    rows = out[:, 0].view(torch.int32)
+    cols = out[:, 1].view(torch.int32)
+    top_r = ((rows >> (k - 1)) & 1).to(torch.int64)
+    top_c = ((cols >> (k - 1)) & 1).to(torch.int64)
+    counts = torch.bincount(2 * top_r + top_c, minlength=4).cpu().numpy().astype(float)
+    p = np.array(G500) / sum(G500)
+    z = (counts - p * m) / np.sqrt(m * p * (1 - p))
+    assert np.all(np.abs(z) < 6), z
+    del out
+    torch.cuda.empty_cache()
+
+
+def test_k34_per_level_chunk_full_size():
+    """One 2^30-edge chunk (edges 31 * 2^30 ..) of the k = 34, per-level noisy,
+    undirected, u64 workload; sampled edges against the oracle."""
+    k, m, ell = 34, 1 << 30, 6
+    P = noisy_levels(k)
+    t = rm.rmat_build_table_levels(P, k, ell, rm.RMAT_UNDIRECTED)
+    groups = oracle.level_groups(P, k, ell)
+    e0 = 31 << 30
+    out = rm.empty_edges(m, k)
+    rm.rmat_generate(t, 34, e0, m, out)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(34)
+    for s in _sample_ranges(m, rng, n=16, width=1024):
+        ref = oracle.generate(groups, k, 34, e0 + s, 1024, undirected=True)
+        assert_same(as_u64_pairs(out[s:s + 1024], k), ref)
+    assert bool((out[:, 0] <= out[:, 1]).all())
+    del out
+    torch.cuda.empty_cache()

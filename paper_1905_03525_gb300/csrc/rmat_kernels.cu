@@ -393,8 +393,8 @@ rmat_status device_props(DeviceProps &out) {
 
 rmat_launch_config_t default_launch_config(const rmat_table *t) {
     rmat_launch_config_t c;
-    c.threads = 512;
-    c.ctas_per_sm = 2;
+    c.threads = 1024;
+    c.ctas_per_sm = 1;
     c.tile_edges = t->k > 32 ? 128 : 256;
     return c;
 }

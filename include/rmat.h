@@ -190,6 +190,35 @@ rmat_status rmat_set_launch_config(rmat_table *t, const rmat_launch_config_t *cf
 rmat_status rmat_get_launch_config(const rmat_table *t, rmat_launch_config_t *cfg);
 
 /* ---------------------------------------------------------------------- */
+/* Batched generation: many graphs, one persistent launch.                 */
+/* ---------------------------------------------------------------------- */
+typedef struct rmat_batch rmat_batch; /* opaque */
+
+/* Create an empty batch. */
+rmat_status rmat_batch_create(rmat_batch **out);
+
+/* Add edges edge_offset .. edge_offset+count-1 of graph (t, seed) written to
+ * `out` (device, 8-byte aligned).  The table must outlive the batch. */
+rmat_status rmat_batch_add(rmat_batch *b, const rmat_table *t, uint64_t seed,
+                           uint64_t edge_offset, uint64_t count, void *out);
+
+/* Pack table images and work list into device memory (synchronous; done
+ * automatically by the first launch).  Call before graph capture.  cfg may be
+ * NULL (default shape); for batches tile_edges must be a multiple of 64.
+ * Adding graphs after preparing discards the device state (and with it any
+ * CUDA graph that captured rmat_batch_launch). */
+rmat_status rmat_batch_prepare(rmat_batch *b, const rmat_launch_config_t *cfg);
+
+/* One persistent launch that generates every added graph.  Capturable in a
+ * CUDA graph after rmat_batch_prepare. */
+rmat_status rmat_batch_launch(rmat_batch *b, rmat_stream_t stream);
+
+/* Number of graphs / total edges in the batch. */
+rmat_status rmat_batch_size(const rmat_batch *b, uint64_t *graphs, uint64_t *edges);
+
+void rmat_batch_free(rmat_batch *b);
+
+/* ---------------------------------------------------------------------- */
 /* Device error flag                                                       */
 /* ---------------------------------------------------------------------- */
 /* Read and clear the device-side error flag (non-zero when a kernel's

@@ -19,7 +19,8 @@ __all__ = [
     "rmat_build_table_levels", "rmat_table_set_flags", "rmat_table_info", "rmat_table_group_info",
     "rmat_table_export", "rmat_table_upload", "rmat_free_table", "rmat_generate", "rmat_generate_host",
     "rmat_generate_naive", "rmat_set_launch_config", "rmat_get_launch_config",
-    "rmat_check_device_errors", "rmat_version", "edge_bytes", "empty_edges",
+    "rmat_check_device_errors", "rmat_version", "edge_bytes", "empty_edges", "Batch", "rmat_batch_create",
+    "rmat_batch_add", "rmat_batch_prepare", "rmat_batch_launch", "rmat_batch_size", "rmat_batch_free",
 ]
 
 
@@ -175,6 +176,65 @@ def rmat_get_launch_config(t: Table) -> dict:
     cfg = LaunchConfig()
     check(lib().rmat_get_launch_config(t.handle, ctypes.byref(cfg)))
     return {"threads": cfg.threads, "ctas_per_sm": cfg.ctas_per_sm, "tile_edges": cfg.tile_edges}
+
+
+class Batch:
+    """Owning handle of an ``rmat_batch``; keeps its tables alive."""
+
+    def __init__(self, handle):
+        self._h = handle
+        self._tables = []
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("batch already freed")
+        return self._h
+
+    def free(self):
+        if self._h:
+            lib().rmat_batch_free(self._h)
+            self._h = None
+            self._tables = []
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def rmat_batch_create() -> Batch:
+    h = ctypes.c_void_p()
+    check(lib().rmat_batch_create(ctypes.byref(h)))
+    return Batch(h)
+
+
+def rmat_batch_add(b: Batch, t: Table, seed: int, edge_offset: int, count: int, out) -> None:
+    check(lib().rmat_batch_add(b.handle, t.handle, seed, edge_offset, count, _ptr(out)))
+    b._tables.append(t)
+
+
+def rmat_batch_prepare(b: Batch, threads=None, ctas_per_sm=None, tile_edges=None) -> None:
+    if threads is None and ctas_per_sm is None and tile_edges is None:
+        check(lib().rmat_batch_prepare(b.handle, None))
+        return
+    cfg = LaunchConfig(threads or 1024, ctas_per_sm or 1, tile_edges or 256)
+    check(lib().rmat_batch_prepare(b.handle, ctypes.byref(cfg)))
+
+
+def rmat_batch_launch(b: Batch, stream=None) -> None:
+    check(lib().rmat_batch_launch(b.handle, _stream(stream)))
+
+
+def rmat_batch_size(b: Batch):
+    g, e = ctypes.c_uint64(), ctypes.c_uint64()
+    check(lib().rmat_batch_size(b.handle, ctypes.byref(g), ctypes.byref(e)))
+    return g.value, e.value
+
+
+def rmat_batch_free(b: Batch) -> None:
+    b.free()
 
 
 def rmat_check_device_errors() -> None:

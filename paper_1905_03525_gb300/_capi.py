@@ -61,6 +61,12 @@ SIGNATURES = [
     ("rmat_generate_naive", _st, [_vp, _i32, _u32, _u64, _u64, _u64, _vp, _vp]),
     ("rmat_set_launch_config", _st, [_vp, _vp]),
     ("rmat_get_launch_config", _st, [_vp, _vp]),
+    ("rmat_batch_create", _st, [_vp]),
+    ("rmat_batch_add", _st, [_vp, _vp, _u64, _u64, _u64, _vp]),
+    ("rmat_batch_prepare", _st, [_vp, _vp]),
+    ("rmat_batch_launch", _st, [_vp, _vp]),
+    ("rmat_batch_size", _st, [_vp, _vp, _vp]),
+    ("rmat_batch_free", None, [_vp]),
     ("rmat_check_device_errors", _st, []),
     ("rmat_version", ctypes.c_char_p, []),
     ("rmat_last_error", ctypes.c_char_p, []),

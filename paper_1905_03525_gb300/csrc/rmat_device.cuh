@@ -39,46 +39,73 @@ __device__ __forceinline__ uint32_t shr_clamp(uint32_t x, uint32_t n) {
     return __funnelshift_rc(x, 0u, n);
 }
 
-template <bool SMEM>
-__device__ __forceinline__ uint32_t ld_word(const uint32_t *p) {
-    if constexpr (SMEM) return *p;
-    else return __ldg(p);
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-template <bool SMEM>
-__device__ __forceinline__ uint4 ld_quad(const uint32_t *p) {
-    if constexpr (SMEM) return *reinterpret_cast<const uint4 *>(p);
-    else return __ldg(reinterpret_cast<const uint4 *>(p));
+__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
 }
 
-// One alias draw from word u: column j = top `bits` bits, residual r = the
-// rest; keep j iff r < thr[j].  A[j] = (thr[j] << bits) | alias[j], and
-// ((u << bits) | mask) < A[j]  <=>  r < thr[j].
-template <bool SMEM>
-__device__ __forceinline__ uint32_t alias_select(const uint32_t *A, uint32_t u, uint32_t bits,
-                                                 uint32_t mask) {
-    const uint32_t j = u >> (32u - bits);
-    const uint32_t a = ld_word<SMEM>(A + j);
-    const uint32_t rs = (u << bits) | mask;
-    return rs < a ? j : (a & mask);
+__device__ __forceinline__ uint4 lds128(uint32_t addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(addr));
+    return v;
 }
 
-// Row bits (left-aligned in 32), column bits (left-aligned) and length of
-// entry `sel`.
-template <int FMT, bool SMEM>
-__device__ __forceinline__ void fetch_path(const uint32_t *B, uint32_t sel, uint32_t &r,
-                                           uint32_t &c, uint32_t &L) {
-    if constexpr (FMT == 0) {
-        const uint32_t p = ld_word<SMEM>(B + sel);
-        r = p & 0xFFF80000u;
-        c = p << 19;
-        L = (p >> 13) & 63u;
-    } else {
-        const uint4 v = ld_quad<SMEM>(B + 4 * sel);
-        r = v.x;
-        c = v.y;
-        L = v.z;
+// Runtime powers of two.  Passing them as kernel arguments keeps them opaque
+// to the compiler, so the bit-field extractions below stay integer multiplies
+// (FMA pipe) instead of shifts and masks on the ALU pipe, which is the busier
+// of the two in these kernels.
+struct Pow2 {
+    uint32_t p6, p13, p19;
+};
+
+// Where one table (group) lives and how to split a word for it.
+template <bool SMEM>
+struct Group {
+    uint32_t sA, sB;             // shared byte addresses of A and B (SMEM)
+    const uint32_t *gA, *gB;     // global addresses (!SMEM)
+    uint32_t mulb, mask;         // 2^b, 2^b - 1
+
+    __device__ __forceinline__ uint32_t a(uint32_t j) const {
+        if constexpr (SMEM) return lds32(sA + 4u * j);
+        else return __ldg(gA + j);
     }
+    __device__ __forceinline__ uint32_t b32(uint32_t i) const {
+        if constexpr (SMEM) return lds32(sB + 4u * i);
+        else return __ldg(gB + i);
+    }
+    __device__ __forceinline__ uint4 b128(uint32_t i) const {
+        if constexpr (SMEM) return lds128(sB + 16u * i);
+        else return __ldg(reinterpret_cast<const uint4 *>(gB) + i);
+    }
+};
+
+// Blob header word `w` (group descriptors), from shared or global memory.
+template <bool SMEM>
+__device__ __forceinline__ uint32_t blob_word(uint32_t sbase, const uint32_t *gblob, uint32_t w) {
+    if constexpr (SMEM) return lds32(sbase + 4u * w);
+    else return __ldg(gblob + w);
+}
+
+template <bool SMEM>
+__device__ __forceinline__ Group<SMEM> group(uint32_t sbase, const uint32_t *gblob, uint32_t g) {
+    Group<SMEM> G;
+    const uint32_t aoff = blob_word<SMEM>(sbase, gblob, g);
+    const uint32_t boff = blob_word<SMEM>(sbase, gblob, 64u + g);
+    const uint32_t bits = blob_word<SMEM>(sbase, gblob, 128u + g);
+    G.sA = sbase + 4u * aoff;
+    G.sB = sbase + 4u * boff;
+    G.gA = gblob + aoff;
+    G.gB = gblob + boff;
+    G.mulb = 1u << bits;
+    G.mask = G.mulb - 1u;
+    return G;
 }
 
 // Left-aligned accumulators.  Appending a path ORs its bits in below the
@@ -87,6 +114,7 @@ __device__ __forceinline__ void fetch_path(const uint32_t *B, uint32_t sel, uint
 struct Acc32 {
     uint32_t row, col, filled;
     __device__ __forceinline__ void clear() { row = col = filled = 0; }
+    // Any number of levels may be appended: shifts of 32 or more give 0.
     __device__ __forceinline__ void append(uint32_t r, uint32_t c, uint32_t L) {
         row |= shr_clamp(r, filled);
         col |= shr_clamp(c, filled);
@@ -110,13 +138,35 @@ struct Acc64 {
     __device__ __forceinline__ uint64_t out_col(int k) const { return col >> (64 - k); }
 };
 
+// One alias draw from word u, appended to acc.
+//   column j = top b bits of u, residual r = the low 32-b bits; one 32x32->64
+//   multiply u * 2^b + (2^b - 1) yields j in the high word and
+//   (r << b) | (2^b - 1) in the low word, and with A[j] = (thr[j] << b) |
+//   alias[j] the draw keeps j iff that low word < A[j]  (<=> r < thr[j]).
+// Compact path entry x: row bits in 31..19, length in 18..13, column bits in
+// 12..0 (both left-aligned in their 13-bit fields).
+template <int FMT, bool SMEM, class Acc>
+__device__ __forceinline__ void draw(const Group<SMEM> &G, const Pow2 &P, uint32_t u, Acc &acc) {
+    const uint64_t t = uint64_t(u) * G.mulb + G.mask;
+    const uint32_t j = uint32_t(t >> 32);
+    const uint32_t rs = uint32_t(t);
+    const uint32_t a = G.a(j);
+    const uint32_t sel = rs < a ? j : (a & G.mask);
+    if constexpr (FMT == 0) {
+        const uint32_t x = G.b32(sel);
+        const uint32_t rowl = __umulhi(x, P.p13) * P.p19;  // bits 31..19, zeros below
+        const uint32_t coll = x * P.p19;                   // bits 12..0 moved to 31..19
+        const uint32_t L = __umulhi(x * P.p13, P.p6);      // bits 18..13
+        acc.append(rowl, coll, L);
+    } else {
+        const uint4 v = G.b128(sel);
+        acc.append(v.x, v.y, v.z);
+    }
+}
+
 // --------------------------------------------------------------------------
 // PTX helpers: mbarrier, TMA bulk copies (global <-> shared), proxy fences.
 // --------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
                  : "memory");
@@ -184,8 +234,8 @@ __device__ __forceinline__ void bulk_wait_all() {
     asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
-// Make this thread's generic-proxy shared-memory writes visible to the async
-// (TMA) proxy.
+// Order this thread's generic-proxy shared-memory accesses before later
+// async-proxy (TMA) accesses.
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }

@@ -15,7 +15,10 @@
 //              {row bits << (32-L), column bits << (32-L), L, 0}
 // Two 4-byte shared-memory loads per draw (A[j], then B[sel]) is the least
 // shared-memory traffic for a random column: each costs one bank access per
-// lane.  Groups are packed back to back, each array 16-byte aligned.
+// lane.  The blob starts with a header of kHeaderWords words -- word g, 64+g
+// and 128+g hold the A offset, B offset and b of group g (offsets in words
+// from the blob start) -- followed by the groups back to back, each array
+// 16-byte aligned, so that one bulk copy stages descriptors and tables.
 #include <algorithm>
 
 #include "rmat_internal.h"
@@ -44,7 +47,7 @@ rmat_status build_image(rmat_table *t) {
     t->format = max_len <= 13 ? kCompact : kWide;
     const size_t bwords = t->format == kCompact ? 1 : 4;
 
-    size_t total = 0;
+    size_t total = kHeaderWords;
     t->gdesc.clear();
     for (const PathTable &g : t->groups) {
         const size_t N = size_t(1) << g.bits;
@@ -61,6 +64,9 @@ rmat_status build_image(rmat_table *t) {
     for (size_t gi = 0; gi < t->groups.size(); ++gi) {
         const PathTable &g = t->groups[gi];
         const GroupDesc &d = t->gdesc[gi];
+        t->image[gi] = d.a_off_words;
+        t->image[kMaxGroups + gi] = d.b_off_words;
+        t->image[2 * kMaxGroups + gi] = uint32_t(g.bits);
         const size_t N = size_t(1) << g.bits;
         uint32_t *A = t->image.data() + d.a_off_words;
         uint32_t *B = t->image.data() + d.b_off_words;

@@ -26,6 +26,9 @@ struct PathTable {
     std::vector<uint32_t> alias;   // alias target
 };
 
+constexpr int kMaxGroups = 64;                 // level groups per table
+constexpr size_t kHeaderWords = 3 * kMaxGroups; // blob header: A offsets, B offsets, bits
+
 // Device table image formats (see rmat_image.cpp).
 enum ImageFormat : int {
     kCompact = 0,  // paths <= 13 levels: A = (thr << b) | alias (u32), B = packed path (u32)

@@ -1,21 +1,24 @@
 // rmat_kernels.cu -- the sampling kernels of librmat (sm_103a) and their
 // launch logic.
 //
-// k_alias: the per-edge sampling loop of arXiv 1905.03525, Sec. 2 (sampling-
-// loop fragment), one edge per lane:
+// gen_tile: the per-edge sampling loop of arXiv 1905.03525, Sec. 2 (sampling-
+// loop fragment) for one warp tile of consecutive edges, two edges per lane:
 //   phase 1  one Philox4x32-10 block (4 words) per edge, up to 4 alias draws,
 //            path bits OR-ed into left-aligned row/column registers;
 //   phase 2  edges that still lack levels after 4 words are queued per warp
 //            (ballot + popc compaction in shared memory) and finished 32 at a
 //            time with further Philox blocks, so that the rare long edges do
 //            not make every lane of a warp pay for a second block.
-// The alias table is staged once per CTA into shared memory by a TMA bulk
-// copy completing on an mbarrier.  Edges are written into a per-warp shared
-// tile and leave with one TMA bulk store per tile (double-buffered, so the
-// store of tile i overlaps the sampling of tile i+1).
-// Per-level tables (Sec. 3, one table per level group) use exactly one draw
+//   Edges are written into a per-warp shared tile that leaves with one TMA
+//   bulk store (double-buffered: the store of one tile overlaps the sampling
+//   of the next).
+// Per-level tables (Sec. 3, one table per level group) take exactly one draw
 // per group, with no phase 2.
 //
+// k_alias: one job (a graph, or a range of one); table blob staged once per
+//          CTA into shared memory by a TMA bulk copy on an mbarrier.
+// k_batch: many jobs in one persistent launch; CTAs pop work units from an
+//          atomic counter and restage the table when the job changes.
 // k_naive: the plain R-MAT process (Sec. 1), one quadrant draw per level.
 #include <algorithm>
 #include <cstdio>
@@ -32,32 +35,13 @@ __device__ unsigned int g_device_error;
 
 namespace {
 
-constexpr int kPendCap = 64;           // per-warp queue of unfinished edges
+constexpr int kPendCap = 64;  // per-warp queue of unfinished edges
 constexpr uint32_t kWaitLimit = 1u << 22;
-constexpr int kMaxGroups = 64;
 
-struct AliasArgs {
-    const uint32_t *image;  // device table image
-    uint32_t image_bytes;   // bytes to stage (multiple of 16); 0 = table read from global
-    uint32_t a_off, b_off;  // group-0 offsets (words)
-    uint32_t bits;
-    int k;
-    int draws1;             // draws in phase 1 (<= 4)
-    int ngroups;            // per-level: number of groups
-    unsigned flags;
-    uint32_t key0, key1;
-    uint64_t e0;            // global index of the first edge
-    uint64_t count;
-    void *out;
-    int tile;               // edges per warp tile
-    unsigned *err;
-};
-
-struct LevelDesc {
-    uint32_t a_off[kMaxGroups];
-    uint32_t b_off[kMaxGroups];
-    uint32_t bits[kMaxGroups];
-};
+// bytes of one warp's shared region: two output tiles and the queue
+__host__ __device__ constexpr uint32_t warp_region_bytes(bool u64, bool levels, int tile) {
+    return 2u * uint32_t(tile) * (u64 ? 16u : 8u) + (levels ? 0u : uint32_t(kPendCap) * (u64 ? 20u : 12u));
+}
 
 template <bool U64>
 struct AccT;
@@ -66,93 +50,37 @@ struct AccT<false> { using type = dev::Acc32; using word = uint32_t; };
 template <>
 struct AccT<true> { using type = dev::Acc64; using word = uint64_t; };
 
+// Where a warp keeps its tiles and queue, and which buffer is next.
+struct WarpState {
+    unsigned char *region;
+    int tile;
+    int buf;
+    bool issued;  // a bulk store is (or may be) in flight
+    int lane;
+};
+
 template <int FMT, bool U64, bool SMEM, bool LEVELS>
-__global__ void __launch_bounds__(1024) k_alias(AliasArgs args, LevelDesc ld) {
+__device__ __forceinline__ void gen_tile(const Job &J, const dev::Pow2 &P, uint32_t sblob, const uint32_t *gblob,
+                                         const dev::Group<SMEM> &G0, uint64_t first, uint32_t n, WarpState &W) {
     using Acc = typename AccT<U64>::type;
     using Word = typename AccT<U64>::word;
     constexpr uint32_t EB = U64 ? 16 : 8;
-    constexpr uint32_t PB = LEVELS ? 0 : kPendCap * (8 + 2 * sizeof(Word));
-
-    extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
-    uint32_t *s_lvl = reinterpret_cast<uint32_t *>(smem + 16);  // 3 x kMaxGroups words
-    unsigned char *s_tab = smem + 16 + (LEVELS ? 3 * kMaxGroups * 4 : 0);
-    const uint32_t tab_bytes = SMEM ? args.image_bytes : 0;
-    unsigned char *s_warps = s_tab + tab_bytes;
-
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
-    const int k = args.k;
-
-    if (LEVELS) {
-        for (int g = threadIdx.x; g < args.ngroups; g += blockDim.x) {
-            s_lvl[g] = ld.a_off[g];
-            s_lvl[kMaxGroups + g] = ld.b_off[g];
-            s_lvl[2 * kMaxGroups + g] = ld.bits[g];
-        }
-    }
-
-    const uint32_t *tab;
-    if constexpr (SMEM) {
-        if (threadIdx.x == 0) {
-            dev::mbar_init(mbar, 1);
-            dev::fence_mbar_init();
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            dev::mbar_arrive_expect_tx(mbar, args.image_bytes);
-            const unsigned char *src = reinterpret_cast<const unsigned char *>(args.image);
-            for (uint32_t off = 0; off < args.image_bytes; off += 32768u) {
-                const uint32_t n = min(32768u, args.image_bytes - off);
-                dev::bulk_g2s(s_tab + off, src + off, n, mbar);
-            }
-        }
-        const bool ok = dev::mbar_wait_bounded(mbar, 0, kWaitLimit);
-        if (!__syncthreads_and(ok)) {
-            if (threadIdx.x == 0) {
-                atomicOr(args.err, 1u);
-                // give the copy in flight a bounded chance to land before exit
-                dev::mbar_wait_bounded(mbar, 0, kWaitLimit);
-            }
-            return;
-        }
-        tab = reinterpret_cast<const uint32_t *>(s_tab);
-    } else {
-        __syncthreads();
-        tab = args.image;
-    }
-
-    const uint32_t bits0 = args.bits;
-    const uint32_t mask0 = (1u << bits0) - 1u;
-    const uint32_t *A0 = tab + args.a_off;
-    const uint32_t *B0 = tab + args.b_off;
-    const int tile = args.tile;
-
-    unsigned char *wreg = s_warps + size_t(warp) * (2 * tile * EB + PB);
-    uint32_t *p_idx = reinterpret_cast<uint32_t *>(wreg + 2 * tile * EB);
-    uint32_t *p_fill = p_idx + kPendCap;
-    Word *p_row = reinterpret_cast<Word *>(p_fill + kPendCap);
+    const int lane = W.lane;
+    const int k = J.k;
+    const uint32_t uk = uint32_t(k);
+    unsigned char *stage = W.region + W.buf * W.tile * EB;
+    uint32_t *p_meta = reinterpret_cast<uint32_t *>(W.region + 2 * W.tile * EB);  // idx | filled << 16
+    Word *p_row = reinterpret_cast<Word *>(p_meta + kPendCap);
     Word *p_col = p_row + kPendCap;
+    const uint64_t ebase = J.e0 + first;
 
-    auto draw = [&](Acc &acc, uint32_t u) {
-        const uint32_t sel = dev::alias_select<SMEM>(A0, u, bits0, mask0);
-        uint32_t r, c, L;
-        dev::fetch_path<FMT, SMEM>(B0, sel, r, c, L);
-        acc.append(r, c, L);
-    };
-    // U32 accumulators tolerate draws past k (shifts clamp, surplus bits
-    // fall off); U64 ones are only extended while short of k.
-    auto draw_guarded = [&](Acc &acc, uint32_t u) {
-        if (U64) {
-            if (acc.filled < uint32_t(k)) draw(acc, u);
-        } else {
-            draw(acc, u);
-        }
-    };
-    auto put = [&](unsigned char *stage, uint32_t idx, const Acc &acc) {
+    // The bulk store issued two tiles ago read this buffer; wait for it.
+    if (lane == 0 && W.issued) dev::bulk_wait_read_1();
+    __syncwarp();
+
+    auto put = [&](uint32_t idx, const Acc &acc) {
         uint64_t r = acc.out_row(k), c = acc.out_col(k);
-        if ((args.flags & RMAT_UNDIRECTED) && r > c) {
+        if ((J.flags & RMAT_UNDIRECTED) && r > c) {
             const uint64_t t = r;
             r = c;
             c = t;
@@ -162,138 +90,275 @@ __global__ void __launch_bounds__(1024) k_alias(AliasArgs args, LevelDesc ld) {
         else
             reinterpret_cast<uint2 *>(stage)[idx] = make_uint2(uint32_t(r), uint32_t(c));
     };
+    // U32 accumulators tolerate draws past k (clamped shifts); U64 ones are
+    // extended only while short of k.
+    auto step = [&](Acc &acc, uint32_t u) {
+        if (!U64 || acc.filled < uk) dev::draw<FMT, SMEM>(G0, P, u, acc);
+    };
 
-    const uint64_t ntiles = (args.count + tile - 1) / tile;
-    const uint64_t stride = uint64_t(gridDim.x) * nwarps;
-    int buf = 0;
-    bool issued = false;
-    for (uint64_t t = uint64_t(blockIdx.x) * nwarps + warp; t < ntiles; t += stride, buf ^= 1) {
-        const uint64_t first = t * tile;
-        const uint64_t left = args.count - first;
-        const uint32_t n = left < uint64_t(tile) ? uint32_t(left) : uint32_t(tile);
-        const uint64_t ebase = args.e0 + first;
-        unsigned char *stage = wreg + buf * tile * EB;
-
-        // The bulk store issued two tiles ago read this buffer; wait for it.
-        if (lane == 0 && issued) dev::bulk_wait_read_1();
-        __syncwarp();
-
-        if constexpr (LEVELS) {
-            for (uint32_t base = 0; base < n; base += 32) {
-                const uint32_t idx = base + lane;
-                const uint64_t e = ebase + idx;
-                Acc acc;
-                acc.clear();
-                for (int q = 0; 4 * q < args.ngroups; ++q) {
-                    const uint4 w = dev::philox(uint32_t(q), 0u, uint32_t(e), uint32_t(e >> 32),
-                                                args.key0, args.key1);
-                    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+    if constexpr (LEVELS) {
+        for (uint32_t base = 0; base < n; base += 32) {
+            const uint32_t idx = base + lane;
+            const uint64_t e = ebase + idx;
+            Acc acc;
+            acc.clear();
+            for (int q = 0; 4 * q < J.ngroups; ++q) {
+                const uint4 w = dev::philox(uint32_t(q), 0u, uint32_t(e), uint32_t(e >> 32), J.key0, J.key1);
+                const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int g = 4 * q + i;
-                        if (g < args.ngroups) {
-                            const uint32_t bg = s_lvl[2 * kMaxGroups + g];
-                            const uint32_t mg = (1u << bg) - 1u;
-                            const uint32_t sel = dev::alias_select<SMEM>(tab + s_lvl[g], ws[i], bg, mg);
-                            uint32_t r, c, L;
-                            dev::fetch_path<FMT, SMEM>(tab + s_lvl[kMaxGroups + g], sel, r, c, L);
-                            acc.append(r, c, L);
-                        }
+                for (int i = 0; i < 4; ++i) {
+                    const int g = 4 * q + i;
+                    if (g < J.ngroups) {
+                        const dev::Group<SMEM> Gg = dev::group<SMEM>(sblob, gblob, uint32_t(g));
+                        dev::draw<FMT, SMEM>(Gg, P, ws[i], acc);
                     }
                 }
-                if (idx < n) put(stage, idx, acc);
             }
-        } else {
-            uint32_t pcount = 0;  // warp-uniform
-            auto finish = [&](uint32_t pbase, uint32_t nb) {
-                // Lanes take queued edges pbase .. pbase+nb-1 and continue
-                // their streams from block 1.
-                const bool has = uint32_t(lane) < nb;
-                Acc acc;
-                acc.clear();
-                acc.filled = uint32_t(k);
-                uint32_t idx = 0;
-                if (has) {
-                    idx = p_idx[pbase + lane];
-                    acc.row = p_row[pbase + lane];
-                    acc.col = p_col[pbase + lane];
-                    acc.filled = p_fill[pbase + lane];
-                }
-                const uint64_t e = ebase + idx;
-                bool more = true;
-                // each draw adds >= 1 level, so at most k draws are ever needed
-                for (uint32_t q = 1; more && q <= 17; ++q) {
-                    const uint4 w = dev::philox(q, 0u, uint32_t(e), uint32_t(e >> 32), args.key0,
-                                                args.key1);
-                    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        if (more && !__any_sync(0xffffffffu, acc.filled < uint32_t(k))) more = false;
-                        if (more && acc.filled < uint32_t(k)) draw(acc, ws[i]);
-                    }
-                }
-                if (has) put(stage, idx, acc);
-            };
-
-            for (uint32_t base = 0; base < uint32_t(tile); base += 32) {
-                const uint32_t idx = base + lane;
-                const bool valid = idx < n;
-                const uint64_t e = ebase + idx;
-                const uint4 w = dev::philox(0u, 0u, uint32_t(e), uint32_t(e >> 32), args.key0, args.key1);
-                Acc acc;
-                acc.clear();
-                draw_guarded(acc, w.x);
-                if (args.draws1 > 1) draw_guarded(acc, w.y);
-                if (args.draws1 > 2) draw_guarded(acc, w.z);
-                if (args.draws1 > 3) draw_guarded(acc, w.w);
-                const bool done = acc.filled >= uint32_t(k);
-                if (valid && done) put(stage, idx, acc);
-                const bool pend = valid && !done;
-                const uint32_t bal = __ballot_sync(0xffffffffu, pend);
-                if (pend) {
-                    const uint32_t pos = pcount + __popc(bal & dev::lane_mask_lt());
-                    p_idx[pos] = idx;
-                    p_row[pos] = acc.row;
-                    p_col[pos] = acc.col;
-                    p_fill[pos] = acc.filled;
-                }
-                pcount += __popc(bal);
-                if (pcount >= 32) {
-                    __syncwarp();
-                    finish(pcount - 32, 32);
-                    pcount -= 32;
-                    __syncwarp();
-                }
-                if (base + 32 >= n) break;
-            }
-            if (pcount) {
-                __syncwarp();
-                finish(0, pcount);
-                __syncwarp();
-            }
+            if (idx < n) put(idx, acc);
         }
-
-        // Store the tile: one TMA bulk copy when aligned, else plain stores.
-        unsigned char *gdst = reinterpret_cast<unsigned char *>(args.out) + first * EB;
-        const uint32_t bytes = n * EB;
-        const bool bulk = ((reinterpret_cast<uintptr_t>(gdst) | bytes) & 15u) == 0;
-        if (bulk) {
-            dev::fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) {
-                dev::bulk_s2g(gdst, stage, bytes);
-                dev::bulk_commit();
+    } else {
+        uint32_t pcount = 0;  // warp-uniform
+        // Lanes take queued edges pbase .. pbase+nb-1 and continue their
+        // streams from block 1.
+        auto finish = [&](uint32_t pbase, uint32_t nb) {
+            const bool has = uint32_t(lane) < nb;
+            Acc acc;
+            acc.clear();
+            acc.filled = uk;
+            uint32_t idx = 0;
+            if (has) {
+                const uint32_t meta = p_meta[pbase + lane];
+                idx = meta & 0xFFFFu;
+                acc.filled = meta >> 16;
+                acc.row = p_row[pbase + lane];
+                acc.col = p_col[pbase + lane];
             }
-            issued = true;
-        } else {
+            const uint64_t e = ebase + idx;
+            bool more = true;
+            // every draw adds >= 1 level, so k <= 64 levels need <= 16 more blocks
+            for (uint32_t q = 1; more && q <= 17; ++q) {
+                const uint4 w = dev::philox(q, 0u, uint32_t(e), uint32_t(e >> 32), J.key0, J.key1);
+                const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (more && !__any_sync(0xffffffffu, acc.filled < uk)) more = false;
+                    if (more && acc.filled < uk) dev::draw<FMT, SMEM>(G0, P, ws[i], acc);
+                }
+            }
+            if (has) put(idx, acc);
+        };
+        auto settle = [&](uint32_t idx, bool valid, const Acc &acc) {
+            const bool done = acc.filled >= uk;
+            if (valid && done) put(idx, acc);
+            const bool pend = valid && !done;
+            const uint32_t bal = __ballot_sync(0xffffffffu, pend);
+            if (pend) {
+                const uint32_t pos = pcount + __popc(bal & dev::lane_mask_lt());
+                p_meta[pos] = idx | (acc.filled << 16);
+                p_row[pos] = acc.row;
+                p_col[pos] = acc.col;
+            }
+            pcount += __popc(bal);
+            if (pcount >= 32) {
+                __syncwarp();
+                finish(pcount - 32, 32);
+                pcount -= 32;
+                __syncwarp();
+            }
+        };
+
+        for (uint32_t base = 0; base < n; base += 64) {
+            const uint32_t i0 = base + lane, i1 = base + 32 + lane;
+            const uint64_t e0 = ebase + i0, e1 = ebase + i1;
+            const uint4 w0 = dev::philox(0u, 0u, uint32_t(e0), uint32_t(e0 >> 32), J.key0, J.key1);
+            const uint4 w1 = dev::philox(0u, 0u, uint32_t(e1), uint32_t(e1 >> 32), J.key0, J.key1);
+            Acc a0, a1;
+            a0.clear();
+            a1.clear();
+            step(a0, w0.x);
+            step(a1, w1.x);
+            if (J.draws1 > 1) {
+                step(a0, w0.y);
+                step(a1, w1.y);
+            }
+            if (J.draws1 > 2) {
+                step(a0, w0.z);
+                step(a1, w1.z);
+            }
+            if (J.draws1 > 3) {
+                step(a0, w0.w);
+                step(a1, w1.w);
+            }
+            settle(i0, i0 < n, a0);
+            settle(i1, i1 < n, a1);
+        }
+        if (pcount) {
             __syncwarp();
-            const uint64_t *src = reinterpret_cast<const uint64_t *>(stage);
-            uint64_t *dst = reinterpret_cast<uint64_t *>(gdst);
-            for (uint32_t i = lane; i < bytes / 8; i += 32) dst[i] = src[i];
+            finish(0, pcount);
             __syncwarp();
         }
     }
-    if (lane == 0 && issued) dev::bulk_wait_all();
+
+    // Store the tile: one TMA bulk copy when aligned, else plain stores.
+    unsigned char *gdst = reinterpret_cast<unsigned char *>(J.out) + first * EB;
+    const uint32_t bytes = n * EB;
+    if (((reinterpret_cast<uintptr_t>(gdst) | bytes) & 15u) == 0) {
+        dev::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            dev::bulk_s2g(gdst, stage, bytes);
+            dev::bulk_commit();
+        }
+        W.issued = true;
+    } else {
+        __syncwarp();
+        const uint64_t *src = reinterpret_cast<const uint64_t *>(stage);
+        uint64_t *dst = reinterpret_cast<uint64_t *>(gdst);
+        for (uint32_t i = lane; i < bytes / 8; i += 32) dst[i] = src[i];
+        __syncwarp();
+    }
+    W.buf ^= 1;
+}
+
+// Stage a blob into shared memory with one bulk copy (chunks of 32 KB) on
+// `mbar`, phase `parity`; every thread returns whether it landed in time.
+__device__ __forceinline__ bool stage_blob(unsigned char *dst, const uint32_t *src, uint32_t bytes, uint64_t *mbar,
+                                           uint32_t parity) {
+    if (threadIdx.x == 0) {
+        dev::fence_proxy_async_smem();
+        dev::mbar_arrive_expect_tx(mbar, bytes);
+        const unsigned char *s = reinterpret_cast<const unsigned char *>(src);
+        for (uint32_t off = 0; off < bytes; off += 32768u) {
+            const uint32_t c = min(32768u, bytes - off);
+            dev::bulk_g2s(dst + off, s + off, c, mbar);
+        }
+    }
+    const bool ok = dev::mbar_wait_bounded(mbar, parity, kWaitLimit);
+    return __syncthreads_and(ok) != 0;
+}
+
+template <int FMT, bool U64, bool SMEM, bool LEVELS>
+__global__ void __launch_bounds__(1024) k_alias(Job J, dev::Pow2 P, int tile, unsigned *err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
+    unsigned char *s_blob = smem + 16;
+    const uint32_t blob_bytes = SMEM ? J.blob_bytes : 0;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+
+    if constexpr (SMEM) {
+        if (threadIdx.x == 0) {
+            dev::mbar_init(mbar, 1);
+            dev::fence_mbar_init();
+        }
+        __syncthreads();
+        if (!stage_blob(s_blob, J.blob, J.blob_bytes, mbar, 0)) {
+            if (threadIdx.x == 0) {
+                atomicOr(err, 1u);
+                dev::mbar_wait_bounded(mbar, 0, kWaitLimit);  // let a late copy land before exit
+            }
+            return;
+        }
+    }
+    const uint32_t sblob = dev::smem_u32(s_blob);
+    const dev::Group<SMEM> G0 = dev::group<SMEM>(sblob, J.blob, 0);
+
+    WarpState W;
+    W.region = s_blob + blob_bytes + size_t(warp) * warp_region_bytes(U64, LEVELS, tile);
+    W.tile = tile;
+    W.buf = 0;
+    W.issued = false;
+    W.lane = lane;
+    const uint64_t ntiles = (J.count + tile - 1) / tile;
+    const uint64_t stride = uint64_t(gridDim.x) * nwarps;
+    for (uint64_t t = uint64_t(blockIdx.x) * nwarps + warp; t < ntiles; t += stride) {
+        const uint64_t first = t * tile;
+        const uint64_t left = J.count - first;
+        const uint32_t n = left < uint64_t(tile) ? uint32_t(left) : uint32_t(tile);
+        gen_tile<FMT, U64, SMEM, LEVELS>(J, P, sblob, J.blob, G0, first, n, W);
+    }
+    if (lane == 0 && W.issued) dev::bulk_wait_all();
+}
+
+// One work unit of a batch: edges [u * unit_edges, ...) of job unit_job[u].
+template <bool U64, int FMT, bool SMEM, bool LEVELS>
+__device__ __forceinline__ void batch_unit(const Job &J, const dev::Pow2 &P, uint32_t sblob, uint64_t local_unit,
+                                           uint64_t unit_edges, int nwarps, int warp, WarpState &W) {
+    const dev::Group<SMEM> G0 = dev::group<SMEM>(sblob, J.blob, 0);
+    const uint64_t f0 = local_unit * unit_edges;
+    const uint64_t end = min(J.count, f0 + unit_edges);
+    for (uint64_t first = f0 + uint64_t(warp) * W.tile; first < end; first += uint64_t(nwarps) * W.tile) {
+        const uint64_t left = end - first;
+        const uint32_t n = left < uint64_t(W.tile) ? uint32_t(left) : uint32_t(W.tile);
+        gen_tile<FMT, U64, SMEM, LEVELS>(J, P, sblob, J.blob, G0, first, n, W);
+    }
+}
+
+template <bool U64>
+__global__ void __launch_bounds__(1024) k_batch(BatchArgs B, dev::Pow2 P) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
+    unsigned long long *s_unit = reinterpret_cast<unsigned long long *>(smem + 8);
+    unsigned char *s_blob = smem + 16;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const uint32_t sblob = dev::smem_u32(s_blob);
+
+    if (threadIdx.x == 0) {
+        dev::mbar_init(mbar, 1);
+        dev::fence_mbar_init();
+    }
+    WarpState W;
+    W.region = s_blob + B.max_blob_bytes + size_t(warp) * warp_region_bytes(U64, false, B.tile);
+    W.tile = B.tile;
+    W.buf = 0;
+    W.issued = false;
+    W.lane = lane;
+
+    const Job *staged = nullptr;
+    uint32_t parity = 0;
+    unsigned long long next = 0;
+    if (threadIdx.x == 0) next = atomicAdd(B.counter, 1ull);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            *s_unit = next;
+            if (next < B.units) next = atomicAdd(B.counter, 1ull);  // prefetch the following unit
+        }
+        __syncthreads();
+        const unsigned long long unit = *s_unit;
+        if (unit >= B.units) break;
+        const uint32_t jid = B.unit_job[unit];
+        const Job *jp = B.jobs + jid;
+        const Job J = *jp;
+        if (J.smem && jp != staged) {
+            // every warp is past the barrier above: nobody reads the old table
+            if (!stage_blob(s_blob, J.blob, J.blob_bytes, mbar, parity)) {
+                if (threadIdx.x == 0) {
+                    atomicOr(B.err, 1u);
+                    dev::mbar_wait_bounded(mbar, parity, kWaitLimit);
+                }
+                break;
+            }
+            parity ^= 1u;
+            staged = jp;
+        }
+        const uint64_t local = unit - J.unit_begin;
+        const int sel = (J.fmt ? 4 : 0) | (J.smem ? 2 : 0) | (J.levels ? 1 : 0);
+        switch (sel) {
+            case 0: batch_unit<U64, 0, false, false>(J, P, sblob, local, B.unit_edges, nwarps, warp, W); break;
+            case 1: batch_unit<U64, 0, false, true>(J, P, sblob, local, B.unit_edges, nwarps, warp, W); break;
+            case 2: batch_unit<U64, 0, true, false>(J, P, sblob, local, B.unit_edges, nwarps, warp, W); break;
+            case 3: batch_unit<U64, 0, true, true>(J, P, sblob, local, B.unit_edges, nwarps, warp, W); break;
+            case 4: batch_unit<U64, 1, false, false>(J, P, sblob, local, B.unit_edges, nwarps, warp, W); break;
+            case 5: batch_unit<U64, 1, false, true>(J, P, sblob, local, B.unit_edges, nwarps, warp, W); break;
+            case 6: batch_unit<U64, 1, true, false>(J, P, sblob, local, B.unit_edges, nwarps, warp, W); break;
+            default: batch_unit<U64, 1, true, true>(J, P, sblob, local, B.unit_edges, nwarps, warp, W); break;
+        }
+        __syncthreads();  // s_unit and the staged table are reused next round
+    }
+    if (lane == 0 && W.issued) dev::bulk_wait_all();
 }
 
 struct NaiveArgs {
@@ -363,6 +428,19 @@ unsigned *device_error_ptr() {
     return static_cast<unsigned *>(p);
 }
 
+dev::Pow2 pow2_consts() {
+    dev::Pow2 P;
+    P.p6 = 1u << 6;
+    P.p13 = 1u << 13;
+    P.p19 = 1u << 19;
+    return P;
+}
+
+cudaError_t set_smem_attr(void *kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+}
+
 }  // namespace
 
 rmat_status device_props(DeviceProps &out) {
@@ -399,27 +477,26 @@ rmat_launch_config_t default_launch_config(const rmat_table *t) {
     return c;
 }
 
+size_t warp_bytes(bool u64, bool levels, int tile) { return warp_region_bytes(u64, levels, tile); }
+
 rmat_status plan_alias_launch(const rmat_table *t, const rmat_launch_config_t &want, AliasPlan &plan) {
     DeviceProps props;
     if (rmat_status st = device_props(props)) return st;
     const bool u64 = t->k > 32;
     const bool levels = t->per_level;
-    const uint32_t EB = u64 ? 16 : 8;
-    const uint32_t PB = levels ? 0 : kPendCap * (8 + 2 * (u64 ? 8 : 4));
-    const uint32_t head = 16 + (levels ? 3 * kMaxGroups * 4 : 0);
-    const uint32_t img = uint32_t(t->image.size() * 4);
+    const size_t img = t->image.size() * 4;
 
     int threads = std::max(128, std::min(1024, want.threads / 32 * 32));
-    int tile = std::max(32, std::min(1024, want.tile_edges / 32 * 32));
-    int ctas = std::max(1, std::min(8, want.ctas_per_sm));
+    int tile = std::max(64, std::min(1024, want.tile_edges / 64 * 64));
+    const int ctas = std::max(1, std::min(8, want.ctas_per_sm));
     auto need = [&](bool smem_table, int th, int tl) {
-        return size_t(head) + (smem_table ? img : 0) + size_t(th / 32) * (2 * size_t(tl) * EB + PB);
+        return size_t(16) + (smem_table ? img : 0) + size_t(th / 32) * warp_region_bytes(u64, levels, tl);
     };
     bool smem_table = true;
-    // shrink tile, then threads, until the table fits next to the warp tiles
+    // shrink the tile, then the CTA, until the table fits beside the warp tiles
     while (need(true, threads, tile) > size_t(props.max_smem)) {
-        if (tile > 64) tile /= 2;
-        else if (threads > 128) threads /= 2;
+        if (tile > 128) tile /= 2;
+        else if (threads > 256) threads /= 2;
         else {
             smem_table = false;
             break;
@@ -427,9 +504,9 @@ rmat_status plan_alias_launch(const rmat_table *t, const rmat_launch_config_t &w
     }
     if (!smem_table) {
         threads = std::max(128, std::min(1024, want.threads / 32 * 32));
-        tile = std::max(32, std::min(1024, want.tile_edges / 32 * 32));
+        tile = std::max(64, std::min(1024, want.tile_edges / 64 * 64));
         while (need(false, threads, tile) > size_t(props.max_smem)) {
-            if (tile > 32) tile /= 2;
+            if (tile > 64) tile /= 2;
             else threads /= 2;
         }
     }
@@ -441,17 +518,11 @@ rmat_status plan_alias_launch(const rmat_table *t, const rmat_launch_config_t &w
     plan.tile = tile;
     plan.smem_bytes = need(smem_table, threads, tile);
     plan.kernel = alias_kernel_table[plan.fmt][u64][smem_table][levels]();
-    if (plan.smem_bytes > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(plan.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(plan.smem_bytes));
-        if (e != cudaSuccess)
-            return fail(RMAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
-    }
+    cudaError_t e = set_smem_attr(plan.kernel, plan.smem_bytes);
+    if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan.kernel, threads,
-                                                                  plan.smem_bytes);
-    if (e != cudaSuccess)
-        return fail(RMAT_ERR_CUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan.kernel, threads, plan.smem_bytes);
+    if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
     if (per_sm < 1) return fail(RMAT_ERR_UNSUPPORTED, "launch shape does not fit on an SM");
     plan.ctas_per_sm = std::min(per_sm, ctas);
     plan.sms = props.sms;
@@ -459,43 +530,68 @@ rmat_status plan_alias_launch(const rmat_table *t, const rmat_launch_config_t &w
     return RMAT_OK;
 }
 
-rmat_status launch_alias(const rmat_table *t, const uint32_t *dimage, const AliasPlan &plan, uint64_t seed,
+Job make_job(const rmat_table *t, const uint32_t *dblob, bool smem, uint64_t seed, uint64_t e0, uint64_t count,
+             void *out) {
+    Job J{};
+    const PathTable &g0 = t->groups[0];
+    J.blob = dblob;
+    J.blob_bytes = uint32_t(t->image.size() * 4);
+    J.k = t->k;
+    const int need_draws = (t->k + std::max(1, g0.min_len) - 1) / std::max(1, g0.min_len);
+    J.draws1 = std::max(1, std::min(4, need_draws));
+    J.ngroups = int(t->groups.size());
+    J.levels = t->per_level ? 1u : 0u;
+    J.flags = t->flags;
+    J.key0 = uint32_t(seed);
+    J.key1 = uint32_t(seed >> 32);
+    J.e0 = e0;
+    J.count = count;
+    J.out = out;
+    J.fmt = uint32_t(t->format);
+    J.smem = smem ? 1u : 0u;
+    J.unit_begin = 0;
+    return J;
+}
+
+rmat_status launch_alias(const rmat_table *t, const uint32_t *dblob, const AliasPlan &plan, uint64_t seed,
                          uint64_t e0, uint64_t count, void *out, cudaStream_t stream) {
     if (count == 0) return RMAT_OK;
-    const PathTable &g0 = t->groups[0];
-    AliasArgs a;
-    a.image = dimage;
-    a.image_bytes = plan.smem_table ? uint32_t(t->image.size() * 4) : 0;
-    a.a_off = t->gdesc[0].a_off_words;
-    a.b_off = t->gdesc[0].b_off_words;
-    a.bits = uint32_t(g0.bits);
-    a.k = t->k;
-    const int need_draws = (t->k + g0.min_len - 1) / std::max(1, g0.min_len);
-    a.draws1 = std::max(1, std::min(4, need_draws));
-    a.ngroups = int(t->groups.size());
-    a.flags = t->flags;
-    a.key0 = uint32_t(seed);
-    a.key1 = uint32_t(seed >> 32);
-    a.e0 = e0;
-    a.count = count;
-    a.out = out;
-    a.tile = plan.tile;
-    a.err = plan.err;
-    LevelDesc ld{};
-    if (t->per_level) {
-        for (size_t g = 0; g < t->gdesc.size(); ++g) {
-            ld.a_off[g] = t->gdesc[g].a_off_words;
-            ld.b_off[g] = t->gdesc[g].b_off_words;
-            ld.bits[g] = uint32_t(t->gdesc[g].bits);
-        }
-    }
+    Job J = make_job(t, dblob, plan.smem_table, seed, e0, count, out);
+    dev::Pow2 P = pow2_consts();
+    int tile = plan.tile;
+    unsigned *err = plan.err;
     const int warps = plan.threads / 32;
     const uint64_t ntiles = (count + plan.tile - 1) / plan.tile;
     const uint64_t want_ctas = (ntiles + warps - 1) / warps;
     const uint64_t max_ctas = uint64_t(plan.sms) * plan.ctas_per_sm;
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want_ctas, max_ctas)));
-    void *params[] = {&a, &ld};
+    void *params[] = {&J, &P, &tile, &err};
     cudaError_t e = cudaLaunchKernel(plan.kernel, dim3(grid), dim3(plan.threads), params, plan.smem_bytes, stream);
+    if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return RMAT_OK;
+}
+
+size_t batch_smem_bytes(bool u64, int threads, int tile, uint32_t max_blob_bytes) {
+    return 16 + size_t(max_blob_bytes) + size_t(threads / 32) * warp_region_bytes(u64, false, tile);
+}
+
+rmat_status batch_occupancy(bool u64, int threads, size_t smem, int &per_sm) {
+    void *fn = u64 ? reinterpret_cast<void *>(&k_batch<true>) : reinterpret_cast<void *>(&k_batch<false>);
+    cudaError_t e = set_smem_attr(fn, smem);
+    if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+    if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
+    return RMAT_OK;
+}
+
+rmat_status launch_batch(bool u64, const BatchArgs &args, int grid, int threads, size_t smem, cudaStream_t stream) {
+    void *fn = u64 ? reinterpret_cast<void *>(&k_batch<true>) : reinterpret_cast<void *>(&k_batch<false>);
+    cudaError_t e = cudaMemsetAsync(args.counter, 0, sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+    BatchArgs a = args;
+    dev::Pow2 P = pow2_consts();
+    void *params[] = {&a, &P};
+    e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), params, smem, stream);
     if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     return RMAT_OK;
 }

@@ -15,12 +15,47 @@ struct DeviceProps {
     unsigned *err = nullptr;  // device error flag
 };
 
+// One generation job: edges e0 .. e0+count-1 of the graph (table blob, seed),
+// written to `out`.  Passed by value to k_alias, read from device memory by
+// k_batch.
+struct Job {
+    const uint32_t *blob;  // device table blob (header + groups)
+    uint32_t blob_bytes;
+    int k;
+    int draws1;            // draws in phase 1 (<= 4)
+    int ngroups;
+    unsigned flags;
+    uint32_t key0, key1;   // Philox key = seed
+    uint64_t e0, count;
+    void *out;
+    uint32_t fmt;          // image format
+    uint32_t smem;         // blob staged in shared memory
+    uint32_t levels;       // draw g uses group g
+    uint64_t unit_begin;   // first work unit of this job (batches)
+};
+
+struct BatchArgs {
+    const Job *jobs;
+    const uint32_t *unit_job;  // job of every work unit
+    uint64_t units;
+    uint64_t unit_edges;
+    unsigned long long *counter;
+    uint32_t max_blob_bytes;   // shared bytes reserved for a staged blob
+    int tile;
+    unsigned *err;
+};
 
 rmat_status device_props(DeviceProps &out);
 rmat_launch_config_t default_launch_config(const rmat_table *t);
 rmat_status plan_alias_launch(const rmat_table *t, const rmat_launch_config_t &want, AliasPlan &plan);
-rmat_status launch_alias(const rmat_table *t, const uint32_t *dimage, const AliasPlan &plan, uint64_t seed,
+Job make_job(const rmat_table *t, const uint32_t *dblob, bool smem, uint64_t seed, uint64_t e0, uint64_t count,
+             void *out);
+rmat_status launch_alias(const rmat_table *t, const uint32_t *dblob, const AliasPlan &plan, uint64_t seed,
                          uint64_t e0, uint64_t count, void *out, cudaStream_t stream);
+size_t warp_bytes(bool u64, bool levels, int tile);
+size_t batch_smem_bytes(bool u64, int threads, int tile, uint32_t max_blob_bytes);
+rmat_status batch_occupancy(bool u64, int threads, size_t smem, int &per_sm);
+rmat_status launch_batch(bool u64, const BatchArgs &args, int grid, int threads, size_t smem, cudaStream_t stream);
 rmat_status launch_naive(const uint32_t *thr3, int k, unsigned flags, uint64_t seed, uint64_t e0,
                          uint64_t count, void *out, cudaStream_t stream);
 rmat_status read_and_clear_device_error(unsigned &value);

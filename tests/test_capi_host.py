@@ -46,7 +46,7 @@ def test_library_exports_every_declared_symbol():
     missing = [n for n in declared_functions() if not hasattr(L, n)]
     assert not missing, missing
     bound = {name for name, _, _ in _capi.SIGNATURES}
-    assert set(declared_functions()) <= bound | {"rmat_no_alloc_placeholder"}
+    assert set(declared_functions()) <= bound
 
 
 def _compare(lib_export, ot):
@@ -91,7 +91,7 @@ def test_table_info():
     info = rm.rmat_table_info(t)
     assert info["entries"] == 4093 and info["bits"] == 12 and info["index_bytes"] == 4
     assert info["max_len"] == 13 and info["groups"] == 1
-    assert info["device_image_bytes"] == 4096 * 8
+    assert info["device_image_bytes"] == 4096 * 8 + 3 * 64 * 4
     t64 = rm.rmat_build_table_levels(noisy_levels(34), 34, 6, rm.RMAT_UNDIRECTED)
     i64 = rm.rmat_table_info(t64)
     assert i64["index_bytes"] == 8 and i64["groups"] == 6 and i64["flags"] == 1
@@ -130,6 +130,19 @@ def test_generate_argument_checks_need_no_device():
         rm.rmat_generate(t, 1, 2 ** 64 - 5, 10, 0x1000)  # index overflow
     assert ei.value.status == _capi.RMAT_ERR_INVALID_ARGUMENT
     rm.rmat_generate(t, 1, 0, 0, 0)               # count == 0 is a no-op
+
+
+def test_batch_host_checks():
+    b = rm.rmat_batch_create()
+    t = rm.rmat_build_table(*G500, 20, 1000)
+    rm.rmat_batch_add(b, t, 1, 0, 100, 0x1000)
+    rm.rmat_batch_add(b, t, 2, 5, 200, 0x2000)
+    assert rm.rmat_batch_size(b) == (2, 300)
+    with pytest.raises(rm.RmatError):
+        rm.rmat_batch_add(b, t, 1, 0, 10, 0x1004)
+    with pytest.raises(rm.RmatError):
+        rm.rmat_batch_add(b, t, 1, 2 ** 64 - 1, 10, 0x1000)
+    b.free()
 
 
 def test_launch_config_roundtrip_and_checks():

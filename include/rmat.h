@@ -204,7 +204,7 @@ rmat_status rmat_batch_add(rmat_batch *b, const rmat_table *t, uint64_t seed,
 
 /* Pack table images and work list into device memory (synchronous; done
  * automatically by the first launch).  Call before graph capture.  cfg may be
- * NULL (default shape); for batches tile_edges must be a multiple of 64.
+ * NULL (default shape).
  * Adding graphs after preparing discards the device state (and with it any
  * CUDA graph that captured rmat_batch_launch). */
 rmat_status rmat_batch_prepare(rmat_batch *b, const rmat_launch_config_t *cfg);

@@ -80,7 +80,7 @@ rmat_status prepare_side(rmat_batch *b, bool u64, const DeviceProps &props, Side
     if (mine.empty()) return RMAT_OK;
 
     int threads = std::max(128, std::min(1024, b->cfg.threads / 32 * 32));
-    int tile = std::max(64, std::min(1024, b->cfg.tile_edges / 64 * 64));
+    int tile = std::max(32, std::min(1024, b->cfg.tile_edges / 32 * 32));
     const size_t per_warp = warp_bytes(u64, false, tile);
     while (16 + size_t(threads / 32) * per_warp > size_t(props.max_smem) && threads > 128) threads /= 2;
     const size_t warps_bytes = size_t(threads / 32) * per_warp;
@@ -189,7 +189,7 @@ rmat_status rmat_batch_prepare(rmat_batch *b, const rmat_launch_config_t *cfg) {
     if (!b) return fail(RMAT_ERR_INVALID_ARGUMENT, "batch is NULL");
     if (cfg) {
         if (cfg->threads < 128 || cfg->threads > 1024 || cfg->threads % 32 || cfg->ctas_per_sm < 1 ||
-            cfg->ctas_per_sm > 8 || cfg->tile_edges < 64 || cfg->tile_edges > 1024 || cfg->tile_edges % 64)
+            cfg->ctas_per_sm > 8 || cfg->tile_edges < 32 || cfg->tile_edges > 1024 || cfg->tile_edges % 32)
             return fail(RMAT_ERR_INVALID_ARGUMENT, "bad batch launch config");
         b->cfg = *cfg;
     }

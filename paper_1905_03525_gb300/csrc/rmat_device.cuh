@@ -34,6 +34,26 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
     return make_uint4(c0, c1, c2, c3);
 }
 
+// The same block function with the ten round keys precomputed (ks[2r],
+// ks[2r+1] = key of round r).  When `ks` lives in a kernel parameter the xors
+// read the round keys straight from the constant bank instead of adding the
+// Weyl constants in registers.
+__device__ __forceinline__ uint4 philox_ks(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                           const uint32_t (&ks)[20]) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t m0 = uint64_t(0xD2511F53u) * c0;
+        const uint64_t m1 = uint64_t(0xCD9E8D57u) * c2;
+        const uint32_t n0 = uint32_t(m1 >> 32) ^ c1 ^ ks[2 * round];
+        const uint32_t n2 = uint32_t(m0 >> 32) ^ c3 ^ ks[2 * round + 1];
+        c1 = uint32_t(m1);
+        c3 = uint32_t(m0);
+        c0 = n0;
+        c2 = n2;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
 // x >> n with n >= 32 giving 0 (one funnel shift).
 __device__ __forceinline__ uint32_t shr_clamp(uint32_t x, uint32_t n) {
     return __funnelshift_rc(x, 0u, n);
@@ -56,14 +76,6 @@ __device__ __forceinline__ uint4 lds128(uint32_t addr) {
                  : "r"(addr));
     return v;
 }
-
-// Runtime powers of two.  Passing them as kernel arguments keeps them opaque
-// to the compiler, so the bit-field extractions below stay integer multiplies
-// (FMA pipe) instead of shifts and masks on the ALU pipe, which is the busier
-// of the two in these kernels.
-struct Pow2 {
-    uint32_t p6, p13, p19;
-};
 
 // Where one table (group) lives and how to split a word for it.
 template <bool SMEM>
@@ -146,7 +158,7 @@ struct Acc64 {
 // Compact path entry x: row bits in 31..19, length in 18..13, column bits in
 // 12..0 (both left-aligned in their 13-bit fields).
 template <int FMT, bool SMEM, class Acc>
-__device__ __forceinline__ void draw(const Group<SMEM> &G, const Pow2 &P, uint32_t u, Acc &acc) {
+__device__ __forceinline__ void draw(const Group<SMEM> &G, uint32_t u, Acc &acc) {
     const uint64_t t = uint64_t(u) * G.mulb + G.mask;
     const uint32_t j = uint32_t(t >> 32);
     const uint32_t rs = uint32_t(t);
@@ -154,10 +166,7 @@ __device__ __forceinline__ void draw(const Group<SMEM> &G, const Pow2 &P, uint32
     const uint32_t sel = rs < a ? j : (a & G.mask);
     if constexpr (FMT == 0) {
         const uint32_t x = G.b32(sel);
-        const uint32_t rowl = __umulhi(x, P.p13) * P.p19;  // bits 31..19, zeros below
-        const uint32_t coll = x * P.p19;                   // bits 12..0 moved to 31..19
-        const uint32_t L = __umulhi(x * P.p13, P.p6);      // bits 18..13
-        acc.append(rowl, coll, L);
+        acc.append(x & 0xFFF80000u, x << 19, (x >> 13) & 63u);
     } else {
         const uint4 v = G.b128(sel);
         acc.append(v.x, v.y, v.z);

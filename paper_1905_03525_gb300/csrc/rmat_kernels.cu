@@ -6,9 +6,9 @@
 //   phase 1  one Philox4x32-10 block (4 words) per edge, up to 4 alias draws,
 //            path bits OR-ed into left-aligned row/column registers;
 //   phase 2  edges that still lack levels after 4 words are queued per warp
-//            (ballot + popc compaction in shared memory) and finished 32 at a
-//            time with further Philox blocks, so that the rare long edges do
-//            not make every lane of a warp pay for a second block.
+//            tile (one warp prefix sum over the lanes' bit masks) and finished
+//            32 at a time with further Philox blocks, so that the rare long
+//            edges do not make every lane of a warp pay for a second block.
 //   Edges are written into a per-warp shared tile that leaves with one TMA
 //   bulk store (double-buffered: the store of one tile overlaps the sampling
 //   of the next).
@@ -35,12 +35,13 @@ __device__ unsigned int g_device_error;
 
 namespace {
 
-constexpr int kPendCap = 64;  // per-warp queue of unfinished edges
 constexpr uint32_t kWaitLimit = 1u << 22;
 
-// bytes of one warp's shared region: two output tiles and the queue
+// Bytes of one warp's shared region: two output tiles, the level count of
+// every unfinished edge (1 byte per edge) and the queue of unfinished edges
+// (2 bytes per edge).
 __host__ __device__ constexpr uint32_t warp_region_bytes(bool u64, bool levels, int tile) {
-    return 2u * uint32_t(tile) * (u64 ? 16u : 8u) + (levels ? 0u : uint32_t(kPendCap) * (u64 ? 20u : 12u));
+    return 2u * uint32_t(tile) * (u64 ? 16u : 8u) + (levels ? 0u : 3u * uint32_t(tile));
 }
 
 template <bool U64>
@@ -59,28 +60,54 @@ struct WarpState {
     int lane;
 };
 
-template <int FMT, bool U64, bool SMEM, bool LEVELS>
-__device__ __forceinline__ void gen_tile(const Job &J, const dev::Pow2 &P, uint32_t sblob, const uint32_t *gblob,
-                                         const dev::Group<SMEM> &G0, uint64_t first, uint32_t n, WarpState &W) {
+// Philox block q of edge e under the job's key.  KS: round keys read from the
+// job's precomputed schedule (kernel parameter), else derived in registers.
+template <bool KS>
+__device__ __forceinline__ uint4 edge_block(const Job &J, uint32_t q, uint64_t e) {
+    if constexpr (KS) return dev::philox_ks(q, 0u, uint32_t(e), uint32_t(e >> 32), J.ks);
+    else return dev::philox(q, 0u, uint32_t(e), uint32_t(e >> 32), J.key0, J.key1);
+}
+
+template <bool U64, bool UNDIR>
+__device__ __forceinline__ void put_final(unsigned char *stage, uint32_t idx, const typename AccT<U64>::type &acc,
+                                          int k) {
+    uint64_t r = acc.out_row(k), c = acc.out_col(k);
+    if (UNDIR && r > c) {
+        const uint64_t t = r;
+        r = c;
+        c = t;
+    }
+    if constexpr (U64)
+        reinterpret_cast<ulonglong2 *>(stage)[idx] = make_ulonglong2(r, c);
+    else
+        reinterpret_cast<uint2 *>(stage)[idx] = make_uint2(uint32_t(r), uint32_t(c));
+}
+
+// Phase 1 over a tile: one Philox block and up to `draws1` draws per edge,
+// two edges per lane in flight (edges it*32 + lane and (it+1)*32 + lane) so
+// that their independent Philox chains and table loads overlap.  Finished
+// edges go to their output slot; unfinished ones leave their raw accumulators
+// in the same slot, their level count in p_fill, and a bit in the lane's mask
+// (bit i = edge i*32 + lane).
+template <int FMT, bool U64, bool SMEM, bool UNDIR, bool FULL, bool KS>
+__device__ __forceinline__ uint32_t phase1(const Job &J, const dev::Group<SMEM> &G0, uint64_t ebase, uint32_t n,
+                                           unsigned char *stage, uint8_t *p_fill, int lane) {
     using Acc = typename AccT<U64>::type;
-    using Word = typename AccT<U64>::word;
-    constexpr uint32_t EB = U64 ? 16 : 8;
-    const int lane = W.lane;
-    const int k = J.k;
-    const uint32_t uk = uint32_t(k);
-    unsigned char *stage = W.region + W.buf * W.tile * EB;
-    uint32_t *p_meta = reinterpret_cast<uint32_t *>(W.region + 2 * W.tile * EB);  // idx | filled << 16
-    Word *p_row = reinterpret_cast<Word *>(p_meta + kPendCap);
-    Word *p_col = p_row + kPendCap;
-    const uint64_t ebase = J.e0 + first;
-
-    // The bulk store issued two tiles ago read this buffer; wait for it.
-    if (lane == 0 && W.issued) dev::bulk_wait_read_1();
-    __syncwarp();
-
-    auto put = [&](uint32_t idx, const Acc &acc) {
-        uint64_t r = acc.out_row(k), c = acc.out_col(k);
-        if ((J.flags & RMAT_UNDIRECTED) && r > c) {
+    const uint32_t uk = uint32_t(J.k);
+    uint32_t pm = 0;
+    const uint32_t iters = (n + 31) / 32;
+    // U32 accumulators tolerate draws past k (clamped shifts); U64 ones are
+    // extended only while short of k.
+    auto step = [&](Acc &acc, uint32_t u) {
+        if (!U64 || acc.filled < uk) dev::draw<FMT, SMEM>(G0, u, acc);
+    };
+    auto settle = [&](const Acc &acc, uint32_t it) {
+        const uint32_t idx = it * 32 + lane;
+        if (!FULL && idx >= n) return;
+        const bool done = acc.filled >= uk;
+        uint64_t r = done ? acc.out_row(J.k) : uint64_t(acc.row);
+        uint64_t c = done ? acc.out_col(J.k) : uint64_t(acc.col);
+        if (UNDIR && done && r > c) {
             const uint64_t t = r;
             r = c;
             c = t;
@@ -89,12 +116,51 @@ __device__ __forceinline__ void gen_tile(const Job &J, const dev::Pow2 &P, uint3
             reinterpret_cast<ulonglong2 *>(stage)[idx] = make_ulonglong2(r, c);
         else
             reinterpret_cast<uint2 *>(stage)[idx] = make_uint2(uint32_t(r), uint32_t(c));
+        p_fill[idx] = uint8_t(acc.filled);
+        pm |= uint32_t(!done) << it;
     };
-    // U32 accumulators tolerate draws past k (clamped shifts); U64 ones are
-    // extended only while short of k.
-    auto step = [&](Acc &acc, uint32_t u) {
-        if (!U64 || acc.filled < uk) dev::draw<FMT, SMEM>(G0, P, u, acc);
-    };
+    for (uint32_t it = 0; it < iters; it += 2) {
+        const uint32_t idx0 = it * 32 + lane;
+        const uint4 w0 = edge_block<KS>(J, 0u, ebase + idx0);
+        const uint4 w1 = edge_block<KS>(J, 0u, ebase + idx0 + 32);
+        Acc a0, a1;
+        a0.clear();
+        a1.clear();
+        step(a0, w0.x);
+        step(a1, w1.x);
+        if (J.draws1 > 1) {
+            step(a0, w0.y);
+            step(a1, w1.y);
+        }
+        if (J.draws1 > 2) {
+            step(a0, w0.z);
+            step(a1, w1.z);
+        }
+        if (J.draws1 > 3) {
+            step(a0, w0.w);
+            step(a1, w1.w);
+        }
+        settle(a0, it);
+        if (it + 1 < iters) settle(a1, it + 1);  // tiles may hold an odd number of 32-edge rows
+    }
+    return pm;
+}
+
+template <int FMT, bool U64, bool SMEM, bool LEVELS, bool UNDIR, bool KS>
+__device__ __forceinline__ void gen_tile(const Job &J, uint32_t sblob, const uint32_t *gblob,
+                                         const dev::Group<SMEM> &G0, uint64_t first, uint32_t n, WarpState &W) {
+    using Acc = typename AccT<U64>::type;
+    constexpr uint32_t EB = U64 ? 16 : 8;
+    const int lane = W.lane;
+    const uint32_t uk = uint32_t(J.k);
+    unsigned char *stage = W.region + W.buf * W.tile * EB;
+    uint8_t *p_fill = W.region + 2 * W.tile * EB;
+    uint16_t *p_q = reinterpret_cast<uint16_t *>(p_fill + W.tile);
+    const uint64_t ebase = J.e0 + first;
+
+    // The bulk store issued two tiles ago read this buffer; wait for it.
+    if (lane == 0 && W.issued) dev::bulk_wait_read_1();
+    __syncwarp();
 
     if constexpr (LEVELS) {
         for (uint32_t base = 0; base < n; base += 32) {
@@ -103,99 +169,77 @@ __device__ __forceinline__ void gen_tile(const Job &J, const dev::Pow2 &P, uint3
             Acc acc;
             acc.clear();
             for (int q = 0; 4 * q < J.ngroups; ++q) {
-                const uint4 w = dev::philox(uint32_t(q), 0u, uint32_t(e), uint32_t(e >> 32), J.key0, J.key1);
+                const uint4 w = edge_block<KS>(J, uint32_t(q), e);
                 const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int g = 4 * q + i;
                     if (g < J.ngroups) {
                         const dev::Group<SMEM> Gg = dev::group<SMEM>(sblob, gblob, uint32_t(g));
-                        dev::draw<FMT, SMEM>(Gg, P, ws[i], acc);
+                        dev::draw<FMT, SMEM>(Gg, ws[i], acc);
                     }
                 }
             }
-            if (idx < n) put(idx, acc);
+            if (idx < n) put_final<U64, UNDIR>(stage, idx, acc, J.k);
         }
     } else {
-        uint32_t pcount = 0;  // warp-uniform
-        // Lanes take queued edges pbase .. pbase+nb-1 and continue their
-        // streams from block 1.
-        auto finish = [&](uint32_t pbase, uint32_t nb) {
-            const bool has = uint32_t(lane) < nb;
-            Acc acc;
-            acc.clear();
-            acc.filled = uk;
-            uint32_t idx = 0;
-            if (has) {
-                const uint32_t meta = p_meta[pbase + lane];
-                idx = meta & 0xFFFFu;
-                acc.filled = meta >> 16;
-                acc.row = p_row[pbase + lane];
-                acc.col = p_col[pbase + lane];
-            }
-            const uint64_t e = ebase + idx;
-            bool more = true;
-            // every draw adds >= 1 level, so k <= 64 levels need <= 16 more blocks
-            for (uint32_t q = 1; more && q <= 17; ++q) {
-                const uint4 w = dev::philox(q, 0u, uint32_t(e), uint32_t(e >> 32), J.key0, J.key1);
-                const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+        const uint32_t pm = n == uint32_t(W.tile)
+                                ? phase1<FMT, U64, SMEM, UNDIR, true, KS>(J, G0, ebase, n, stage, p_fill, lane)
+                                : phase1<FMT, U64, SMEM, UNDIR, false, KS>(J, G0, ebase, n, stage, p_fill, lane);
+        // Phase 2: queue the unfinished edges of the whole tile (warp prefix
+        // sum of the lanes' counts), then finish them 32 at a time.
+        const uint32_t cnt = __popc(pm);
+        uint32_t incl = cnt;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    if (more && !__any_sync(0xffffffffu, acc.filled < uk)) more = false;
-                    if (more && acc.filled < uk) dev::draw<FMT, SMEM>(G0, P, ws[i], acc);
-                }
-            }
-            if (has) put(idx, acc);
-        };
-        auto settle = [&](uint32_t idx, bool valid, const Acc &acc) {
-            const bool done = acc.filled >= uk;
-            if (valid && done) put(idx, acc);
-            const bool pend = valid && !done;
-            const uint32_t bal = __ballot_sync(0xffffffffu, pend);
-            if (pend) {
-                const uint32_t pos = pcount + __popc(bal & dev::lane_mask_lt());
-                p_meta[pos] = idx | (acc.filled << 16);
-                p_row[pos] = acc.row;
-                p_col[pos] = acc.col;
-            }
-            pcount += __popc(bal);
-            if (pcount >= 32) {
-                __syncwarp();
-                finish(pcount - 32, 32);
-                pcount -= 32;
-                __syncwarp();
-            }
-        };
-
-        for (uint32_t base = 0; base < n; base += 64) {
-            const uint32_t i0 = base + lane, i1 = base + 32 + lane;
-            const uint64_t e0 = ebase + i0, e1 = ebase + i1;
-            const uint4 w0 = dev::philox(0u, 0u, uint32_t(e0), uint32_t(e0 >> 32), J.key0, J.key1);
-            const uint4 w1 = dev::philox(0u, 0u, uint32_t(e1), uint32_t(e1 >> 32), J.key0, J.key1);
-            Acc a0, a1;
-            a0.clear();
-            a1.clear();
-            step(a0, w0.x);
-            step(a1, w1.x);
-            if (J.draws1 > 1) {
-                step(a0, w0.y);
-                step(a1, w1.y);
-            }
-            if (J.draws1 > 2) {
-                step(a0, w0.z);
-                step(a1, w1.z);
-            }
-            if (J.draws1 > 3) {
-                step(a0, w0.w);
-                step(a1, w1.w);
-            }
-            settle(i0, i0 < n, a0);
-            settle(i1, i1 < n, a1);
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
         }
-        if (pcount) {
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total) {
+            uint32_t pos = incl - cnt;
+            for (uint32_t m = pm; m; m &= m - 1) p_q[pos++] = uint16_t((__ffs(m) - 1) * 32 + lane);
             __syncwarp();
-            finish(0, pcount);
-            __syncwarp();
+            for (uint32_t pb = 0; pb < total; pb += 32) {
+                const bool has = pb + lane < total;
+                Acc acc;
+                acc.clear();
+                acc.filled = uk;
+                uint32_t idx = 0;
+                if (has) {
+                    idx = p_q[pb + lane];
+                    if constexpr (U64) {
+                        const ulonglong2 v = reinterpret_cast<const ulonglong2 *>(stage)[idx];
+                        acc.row = v.x;
+                        acc.col = v.y;
+                    } else {
+                        const uint2 v = reinterpret_cast<const uint2 *>(stage)[idx];
+                        acc.row = v.x;
+                        acc.col = v.y;
+                    }
+                    acc.filled = p_fill[idx];
+                }
+                const uint64_t e = ebase + idx;
+                // every draw adds >= 1 level, so k <= 64 levels need <= 16 more
+                // blocks; the loop leaves as soon as no lane of the warp needs
+                // another draw (a warp-uniform branch)
+                for (uint32_t q = 1; q <= 17; ++q) {
+                    if (!__any_sync(0xffffffffu, acc.filled < uk)) break;
+                    const uint4 w = edge_block<KS>(J, q, e);
+                    if (U64) {
+                        if (acc.filled < uk) dev::draw<FMT, SMEM>(G0, w.x, acc);
+                    } else {
+                        dev::draw<FMT, SMEM>(G0, w.x, acc);
+                    }
+                    if (!__any_sync(0xffffffffu, acc.filled < uk)) break;
+                    if (!U64 || acc.filled < uk) dev::draw<FMT, SMEM>(G0, w.y, acc);
+                    if (!__any_sync(0xffffffffu, acc.filled < uk)) break;
+                    if (!U64 || acc.filled < uk) dev::draw<FMT, SMEM>(G0, w.z, acc);
+                    if (!__any_sync(0xffffffffu, acc.filled < uk)) break;
+                    if (!U64 || acc.filled < uk) dev::draw<FMT, SMEM>(G0, w.w, acc);
+                }
+                if (has) put_final<U64, UNDIR>(stage, idx, acc, J.k);
+            }
         }
     }
 
@@ -237,8 +281,8 @@ __device__ __forceinline__ bool stage_blob(unsigned char *dst, const uint32_t *s
     return __syncthreads_and(ok) != 0;
 }
 
-template <int FMT, bool U64, bool SMEM, bool LEVELS>
-__global__ void __launch_bounds__(1024) k_alias(Job J, dev::Pow2 P, int tile, unsigned *err) {
+template <int FMT, bool U64, bool SMEM, bool LEVELS, bool UNDIR>
+__global__ void __launch_bounds__(1024) k_alias(const __grid_constant__ Job J, int tile, unsigned *err) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
     unsigned char *s_blob = smem + 16;
@@ -276,27 +320,27 @@ __global__ void __launch_bounds__(1024) k_alias(Job J, dev::Pow2 P, int tile, un
         const uint64_t first = t * tile;
         const uint64_t left = J.count - first;
         const uint32_t n = left < uint64_t(tile) ? uint32_t(left) : uint32_t(tile);
-        gen_tile<FMT, U64, SMEM, LEVELS>(J, P, sblob, J.blob, G0, first, n, W);
+        gen_tile<FMT, U64, SMEM, LEVELS, UNDIR, true>(J, sblob, J.blob, G0, first, n, W);
     }
     if (lane == 0 && W.issued) dev::bulk_wait_all();
 }
 
 // One work unit of a batch: edges [u * unit_edges, ...) of job unit_job[u].
-template <bool U64, int FMT, bool SMEM, bool LEVELS>
-__device__ __forceinline__ void batch_unit(const Job &J, const dev::Pow2 &P, uint32_t sblob, uint64_t local_unit,
-                                           uint64_t unit_edges, int nwarps, int warp, WarpState &W) {
+template <bool U64, int FMT, bool SMEM, bool LEVELS, bool UNDIR>
+__device__ __forceinline__ void batch_unit(const Job &J, uint32_t sblob, uint64_t local_unit, uint64_t unit_edges,
+                                           int nwarps, int warp, WarpState &W) {
     const dev::Group<SMEM> G0 = dev::group<SMEM>(sblob, J.blob, 0);
     const uint64_t f0 = local_unit * unit_edges;
     const uint64_t end = min(J.count, f0 + unit_edges);
     for (uint64_t first = f0 + uint64_t(warp) * W.tile; first < end; first += uint64_t(nwarps) * W.tile) {
         const uint64_t left = end - first;
         const uint32_t n = left < uint64_t(W.tile) ? uint32_t(left) : uint32_t(W.tile);
-        gen_tile<FMT, U64, SMEM, LEVELS>(J, P, sblob, J.blob, G0, first, n, W);
+        gen_tile<FMT, U64, SMEM, LEVELS, UNDIR, false>(J, sblob, J.blob, G0, first, n, W);
     }
 }
 
 template <bool U64>
-__global__ void __launch_bounds__(1024) k_batch(BatchArgs B, dev::Pow2 P) {
+__global__ void __launch_bounds__(1024) k_batch(BatchArgs B) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
     unsigned long long *s_unit = reinterpret_cast<unsigned long long *>(smem + 8);
@@ -345,17 +389,27 @@ __global__ void __launch_bounds__(1024) k_batch(BatchArgs B, dev::Pow2 P) {
             staged = jp;
         }
         const uint64_t local = unit - J.unit_begin;
-        const int sel = (J.fmt ? 4 : 0) | (J.smem ? 2 : 0) | (J.levels ? 1 : 0);
+        const int sel = (J.fmt ? 8 : 0) | (J.smem ? 4 : 0) | (J.levels ? 2 : 0) | ((J.flags & RMAT_UNDIRECTED) ? 1 : 0);
+#define RMAT_UNIT(F, S, L, U) batch_unit<U64, F, S, L, U>(J, sblob, local, B.unit_edges, nwarps, warp, W)
         switch (sel) {
-            case 0: batch_unit<U64, 0, false, false>(J, P, sblob, local, B.unit_edges, nwarps, warp, W); break;
-            case 1: batch_unit<U64, 0, false, true>(J, P, sblob, local, B.unit_edges, nwarps, warp, W); break;
-            case 2: batch_unit<U64, 0, true, false>(J, P, sblob, local, B.unit_edges, nwarps, warp, W); break;
-            case 3: batch_unit<U64, 0, true, true>(J, P, sblob, local, B.unit_edges, nwarps, warp, W); break;
-            case 4: batch_unit<U64, 1, false, false>(J, P, sblob, local, B.unit_edges, nwarps, warp, W); break;
-            case 5: batch_unit<U64, 1, false, true>(J, P, sblob, local, B.unit_edges, nwarps, warp, W); break;
-            case 6: batch_unit<U64, 1, true, false>(J, P, sblob, local, B.unit_edges, nwarps, warp, W); break;
-            default: batch_unit<U64, 1, true, true>(J, P, sblob, local, B.unit_edges, nwarps, warp, W); break;
+            case 0: RMAT_UNIT(0, false, false, false); break;
+            case 1: RMAT_UNIT(0, false, false, true); break;
+            case 2: RMAT_UNIT(0, false, true, false); break;
+            case 3: RMAT_UNIT(0, false, true, true); break;
+            case 4: RMAT_UNIT(0, true, false, false); break;
+            case 5: RMAT_UNIT(0, true, false, true); break;
+            case 6: RMAT_UNIT(0, true, true, false); break;
+            case 7: RMAT_UNIT(0, true, true, true); break;
+            case 8: RMAT_UNIT(1, false, false, false); break;
+            case 9: RMAT_UNIT(1, false, false, true); break;
+            case 10: RMAT_UNIT(1, false, true, false); break;
+            case 11: RMAT_UNIT(1, false, true, true); break;
+            case 12: RMAT_UNIT(1, true, false, false); break;
+            case 13: RMAT_UNIT(1, true, false, true); break;
+            case 14: RMAT_UNIT(1, true, true, false); break;
+            default: RMAT_UNIT(1, true, true, true); break;
         }
+#undef RMAT_UNIT
         __syncthreads();  // s_unit and the staged table are reused next round
     }
     if (lane == 0 && W.issued) dev::bulk_wait_all();
@@ -403,21 +457,21 @@ __global__ void __launch_bounds__(256) k_naive(NaiveArgs a) {
     }
 }
 
-template <int FMT, bool U64, bool SMEM, bool LEVELS>
+template <int FMT, bool U64, bool SMEM, bool LEVELS, bool UNDIR>
 void *alias_kernel_ptr() {
-    return reinterpret_cast<void *>(&k_alias<FMT, U64, SMEM, LEVELS>);
+    return reinterpret_cast<void *>(&k_alias<FMT, U64, SMEM, LEVELS, UNDIR>);
 }
 
 using KernelFn = void *(*)();
-KernelFn alias_kernel_table[2][2][2][2] = {
-    {{{alias_kernel_ptr<0, false, false, false>, alias_kernel_ptr<0, false, false, true>},
-      {alias_kernel_ptr<0, false, true, false>, alias_kernel_ptr<0, false, true, true>}},
-     {{alias_kernel_ptr<0, true, false, false>, alias_kernel_ptr<0, true, false, true>},
-      {alias_kernel_ptr<0, true, true, false>, alias_kernel_ptr<0, true, true, true>}}},
-    {{{alias_kernel_ptr<1, false, false, false>, alias_kernel_ptr<1, false, false, true>},
-      {alias_kernel_ptr<1, false, true, false>, alias_kernel_ptr<1, false, true, true>}},
-     {{alias_kernel_ptr<1, true, false, false>, alias_kernel_ptr<1, true, false, true>},
-      {alias_kernel_ptr<1, true, true, false>, alias_kernel_ptr<1, true, true, true>}}}};
+#define RMAT_K2(F, U, S, L) {alias_kernel_ptr<F, U, S, L, false>, alias_kernel_ptr<F, U, S, L, true>}
+#define RMAT_K4(F, U, S) {RMAT_K2(F, U, S, false), RMAT_K2(F, U, S, true)}
+#define RMAT_K8(F, U) {RMAT_K4(F, U, false), RMAT_K4(F, U, true)}
+// [format][u64][shared table][per-level][undirected]
+KernelFn alias_kernel_table[2][2][2][2][2] = {{RMAT_K8(0, false), RMAT_K8(0, true)},
+                                              {RMAT_K8(1, false), RMAT_K8(1, true)}};
+#undef RMAT_K8
+#undef RMAT_K4
+#undef RMAT_K2
 
 std::mutex g_props_mu;
 std::vector<DeviceProps> g_props;
@@ -426,14 +480,6 @@ unsigned *device_error_ptr() {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_device_error) != cudaSuccess) return nullptr;
     return static_cast<unsigned *>(p);
-}
-
-dev::Pow2 pow2_consts() {
-    dev::Pow2 P;
-    P.p6 = 1u << 6;
-    P.p13 = 1u << 13;
-    P.p19 = 1u << 19;
-    return P;
 }
 
 cudaError_t set_smem_attr(void *kernel, size_t bytes) {
@@ -487,7 +533,7 @@ rmat_status plan_alias_launch(const rmat_table *t, const rmat_launch_config_t &w
     const size_t img = t->image.size() * 4;
 
     int threads = std::max(128, std::min(1024, want.threads / 32 * 32));
-    int tile = std::max(64, std::min(1024, want.tile_edges / 64 * 64));
+    int tile = std::max(32, std::min(1024, want.tile_edges / 32 * 32));
     const int ctas = std::max(1, std::min(8, want.ctas_per_sm));
     auto need = [&](bool smem_table, int th, int tl) {
         return size_t(16) + (smem_table ? img : 0) + size_t(th / 32) * warp_region_bytes(u64, levels, tl);
@@ -504,9 +550,9 @@ rmat_status plan_alias_launch(const rmat_table *t, const rmat_launch_config_t &w
     }
     if (!smem_table) {
         threads = std::max(128, std::min(1024, want.threads / 32 * 32));
-        tile = std::max(64, std::min(1024, want.tile_edges / 64 * 64));
+        tile = std::max(32, std::min(1024, want.tile_edges / 32 * 32));
         while (need(false, threads, tile) > size_t(props.max_smem)) {
-            if (tile > 64) tile /= 2;
+            if (tile > 32) tile /= 2;
             else threads /= 2;
         }
     }
@@ -517,7 +563,7 @@ rmat_status plan_alias_launch(const rmat_table *t, const rmat_launch_config_t &w
     plan.threads = threads;
     plan.tile = tile;
     plan.smem_bytes = need(smem_table, threads, tile);
-    plan.kernel = alias_kernel_table[plan.fmt][u64][smem_table][levels]();
+    plan.kernel = alias_kernel_table[plan.fmt][u64][smem_table][levels][(t->flags & RMAT_UNDIRECTED) ? 1 : 0]();
     cudaError_t e = set_smem_attr(plan.kernel, plan.smem_bytes);
     if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
     int per_sm = 0;
@@ -544,6 +590,10 @@ Job make_job(const rmat_table *t, const uint32_t *dblob, bool smem, uint64_t see
     J.flags = t->flags;
     J.key0 = uint32_t(seed);
     J.key1 = uint32_t(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        J.ks[2 * r] = J.key0 + uint32_t(r) * 0x9E3779B9u;
+        J.ks[2 * r + 1] = J.key1 + uint32_t(r) * 0xBB67AE85u;
+    }
     J.e0 = e0;
     J.count = count;
     J.out = out;
@@ -557,7 +607,6 @@ rmat_status launch_alias(const rmat_table *t, const uint32_t *dblob, const Alias
                          uint64_t e0, uint64_t count, void *out, cudaStream_t stream) {
     if (count == 0) return RMAT_OK;
     Job J = make_job(t, dblob, plan.smem_table, seed, e0, count, out);
-    dev::Pow2 P = pow2_consts();
     int tile = plan.tile;
     unsigned *err = plan.err;
     const int warps = plan.threads / 32;
@@ -565,7 +614,7 @@ rmat_status launch_alias(const rmat_table *t, const uint32_t *dblob, const Alias
     const uint64_t want_ctas = (ntiles + warps - 1) / warps;
     const uint64_t max_ctas = uint64_t(plan.sms) * plan.ctas_per_sm;
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want_ctas, max_ctas)));
-    void *params[] = {&J, &P, &tile, &err};
+    void *params[] = {&J, &tile, &err};
     cudaError_t e = cudaLaunchKernel(plan.kernel, dim3(grid), dim3(plan.threads), params, plan.smem_bytes, stream);
     if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     return RMAT_OK;
@@ -589,8 +638,7 @@ rmat_status launch_batch(bool u64, const BatchArgs &args, int grid, int threads,
     cudaError_t e = cudaMemsetAsync(args.counter, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     BatchArgs a = args;
-    dev::Pow2 P = pow2_consts();
-    void *params[] = {&a, &P};
+    void *params[] = {&a};
     e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), params, smem, stream);
     if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     return RMAT_OK;

@@ -121,7 +121,8 @@ def test_launch_shape_does_not_change_output():
     k, m = 26, (1 << 17) + 5
     t = rm.rmat_build_table(*G500, k, 4096)
     ref = gpu_edges(t, k, 8, 0, m)
-    for threads, ctas, tile in [(128, 1, 32), (256, 4, 64), (512, 2, 1024), (1024, 1, 256), (1024, 1, 512)]:
+    for threads, ctas, tile in [(128, 1, 32), (256, 4, 64), (256, 2, 96), (512, 1, 160), (512, 2, 1024),
+                                (1024, 1, 256), (1024, 1, 512)]:
         rm.rmat_set_launch_config(t, threads, ctas, tile)
         assert_same(gpu_edges(t, k, 8, 0, m), ref)
 

@@ -219,6 +219,41 @@ rmat_status rmat_batch_size(const rmat_batch *b, uint64_t *graphs, uint64_t *edg
 void rmat_batch_free(rmat_batch *b);
 
 /* ---------------------------------------------------------------------- */
+/* Generation without device allocation                                    */
+/* ---------------------------------------------------------------------- */
+/* The paper has no counterpart to this call; it serves callers that cannot
+ * allocate device memory -- a process whose device memory is already
+ * reserved by another framework's caching allocator, a latency-critical path
+ * that must not take the driver's allocation locks (cudaMalloc/cudaFree can
+ * synchronise the device), or a deployment with a fixed memory budget.
+ *
+ * rmat_generate_batch_noalloc -- the batched generation of rmat_batch_launch
+ * for n graphs (tables[i], seeds[i]): edges edge_offsets[i] ..
+ * edge_offsets[i]+counts[i]-1 into outs[i] (device, 8-byte aligned).  It
+ * calls no cudaMalloc/cudaFree and allocates no host memory: the work
+ * counter, job list, unit map and copies of the table blobs live in one
+ * library-owned device array of RMAT_NOALLOC_SCRATCH_BYTES, which every GPU
+ * that loads the library keeps until the process exits.
+ *   - n <= RMAT_NOALLOC_MAX_GRAPHS; all tables of one call have the same
+ *     output width (all k <= 32 or all k > 32); their blobs, the job list and
+ *     one 4-byte entry per 32768 edges (16384 for k > 32) must fit the scratch.
+ *     Anything larger returns RMAT_ERR_INVALID_ARGUMENT and launches nothing.
+ *   - The first call on a device looks up the scratch's device address (once
+ *     per device, with that device current); make that first call before any
+ *     stream capture.
+ *   - Asynchronous on `stream`.  Every call shares the one scratch array and
+ *     overwrites it (the work counter is cleared each call): calls whose work
+ *     overlaps on the GPU -- on different streams, or from threads that race
+ *     -- corrupt each other.  Order them on one stream or synchronise.
+ * Output bytes are identical to rmat_generate / rmat_batch_launch for the same
+ * (table, seed, edge index). */
+#define RMAT_NOALLOC_SCRATCH_BYTES (4u << 20)
+#define RMAT_NOALLOC_MAX_GRAPHS 64u
+rmat_status rmat_generate_batch_noalloc(const rmat_table *const *tables, const uint64_t *seeds,
+                                        const uint64_t *edge_offsets, const uint64_t *counts,
+                                        void *const *outs, uint32_t n, rmat_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
 /* Device error flag                                                       */
 /* ---------------------------------------------------------------------- */
 /* Read and clear the device-side error flag (non-zero when a kernel's

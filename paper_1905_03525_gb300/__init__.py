@@ -21,6 +21,7 @@ __all__ = [
     "rmat_generate_naive", "rmat_set_launch_config", "rmat_get_launch_config",
     "rmat_check_device_errors", "rmat_version", "edge_bytes", "empty_edges", "Batch", "rmat_batch_create",
     "rmat_batch_add", "rmat_batch_prepare", "rmat_batch_launch", "rmat_batch_size", "rmat_batch_free",
+    "rmat_generate_batch_noalloc",
 ]
 
 
@@ -235,6 +236,20 @@ def rmat_batch_size(b: Batch):
 
 def rmat_batch_free(b: Batch) -> None:
     b.free()
+
+
+def rmat_generate_batch_noalloc(tables, seeds, edge_offsets, counts, outs, stream=None) -> None:
+    """Batched generation that allocates no device memory (scratch lives in a
+    fixed library array; see include/rmat.h for the limits)."""
+    n = len(tables)
+    if not (len(seeds) == len(edge_offsets) == len(counts) == len(outs) == n):
+        raise ValueError("argument lists differ in length")
+    T = (ctypes.c_void_p * max(n, 1))(*[t.handle.value for t in tables])
+    S = (ctypes.c_uint64 * max(n, 1))(*seeds)
+    E = (ctypes.c_uint64 * max(n, 1))(*edge_offsets)
+    C = (ctypes.c_uint64 * max(n, 1))(*counts)
+    O = (ctypes.c_void_p * max(n, 1))(*[_ptr(o) for o in outs])
+    check(lib().rmat_generate_batch_noalloc(T, S, E, C, O, n, _stream(stream)))
 
 
 def rmat_check_device_errors() -> None:

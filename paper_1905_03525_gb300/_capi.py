@@ -67,6 +67,7 @@ SIGNATURES = [
     ("rmat_batch_launch", _st, [_vp, _vp]),
     ("rmat_batch_size", _st, [_vp, _vp, _vp]),
     ("rmat_batch_free", None, [_vp]),
+    ("rmat_generate_batch_noalloc", _st, [_vp, _vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
     ("rmat_check_device_errors", _st, []),
     ("rmat_version", ctypes.c_char_p, []),
     ("rmat_last_error", ctypes.c_char_p, []),

@@ -46,6 +46,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-edges", type=int, default=1 << 27)
+    ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5"], default="c2",
+                    help="c2 (default): the contract line; c1/c3/c4/c5: the other configurations, one JSON line each")
+    ap.add_argument("--graphs", type=int, default=4096, help="c4: number of graphs")
+    ap.add_argument("--wave-gib", type=float, default=48.0, help="c4: output budget per batched launch")
+    ap.add_argument("--requests", type=int, default=256, help="c5: trace length")
+    ap.add_argument("--rate", type=float, default=2000.0, help="c5: mean arrivals per second")
     return ap.parse_args()
 
 
@@ -233,6 +239,12 @@ def run_ours(args):
     achieved = 8.0 * m / avg_launch_s / 1e9
     rm.rmat_check_device_errors()
 
+    # comparator: the naive per-bit kernel (k quadrant draws per edge) on the same workload
+    naive_s = _events_time(lambda: rm.rmat_generate_naive(G500, K, 0, SEED, e0, m, out, stream), stream, 2)
+    # restore this step's output of the alias kernel
+    rm.rmat_generate(table, SEED, e0, m, out, stream)
+    stream.synchronize()
+
     # end to end through the public host-buffer call: table built and uploaded
     # every step (h2d), all edges copied back into pinned host memory (d2h).
     e2e = None
@@ -276,6 +288,8 @@ def run_ours(args):
                      "traffic": None, "peak_source": f"{peak_src} hbm_gbs (copy)",
                      "algorithmic_bytes_per_launch": 8 * m, "avg_launch_ms": avg_launch_s * 1e3},
         "cpu_baseline": cb,
+        "comparators": {"naive_per_bit_gpu": {"value": world * m / naive_s, "unit": "edges/s",
+                                              "note": "k Philox words and quadrant draws per edge, same GPU"}},
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": {"sm_mhz": cs["sm_mhz"], "sm_max_mhz": cs["sm_max_mhz"], "reasons": cs["reasons"]},
@@ -285,10 +299,164 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _events_time(fn, stream, reps):
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    stream.synchronize()
+    return a.elapsed_time(b) / 1e3 / reps
+
+
+def run_c1(args):
+    """k=16, m=2^20, fixed l=4 (256-entry table), seed 1: one launch per step."""
+    import torch
+    import paper_1905_03525_gb300 as rm
+    k, m = 16, 1 << 20
+    t = rm.rmat_build_table_fixed(*G500, k, 4)
+    rm.rmat_table_upload(t)
+    out = rm.empty_edges(m, k)
+    s = torch.cuda.Stream()
+    for _ in range(max(3, args.warmup)):
+        rm.rmat_generate(t, 1, 0, m, out, s)
+    dt = _events_time(lambda: rm.rmat_generate(t, 1, 0, m, out, s), s, max(args.steps, 50))
+    # the same launch replayed from a CUDA graph (no host launch cost)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        for _ in range(20):
+            rm.rmat_generate(t, 1, 0, m, out, s)
+    g.replay()
+    dtg = _events_time(g.replay, s, 5) / 20
+    print(json.dumps({"workload": "c1", "config": {"workload": "R-MAT k=16, m=2^20, fixed l=4 (256 entries), "
+                      "a,b,c,d=0.57,0.19,0.19,0.05, seed=1, u32"}, "metric": "edges/s", "value": m / dt,
+                      "ms_per_launch": dt * 1e3, "graph_replay_edges_per_s": m / dtg,
+                      "graph_replay_us_per_launch": dtg * 1e6, "hbm_gbs": 8 * m / dtg / 1e9}), flush=True)
+
+
+def run_c3(args):
+    """k=34, m=2^35 in 32 chunks of 2^30 edges, u64 pairs, undirected, per-level
+    noisy parameters, one table per level group (group length tuned)."""
+    import torch
+    import paper_1905_03525_gb300 as rm
+    from paper_1905_03525_gb300 import autotune
+    from paper_1905_03525_gb300.workloads import noisy_levels
+    k, chunk, nchunks = 34, 1 << 30, 32
+    P = noisy_levels(k)
+    choice = autotune.tune_levels(k, P, rm.RMAT_UNDIRECTED)
+    t = rm.rmat_build_table_levels(P, k, choice["ell"], rm.RMAT_UNDIRECTED)
+    shape, _ = autotune.tune_launch(t, sample_edges=1 << 26)
+    out = rm.empty_edges(chunk, k)
+    s = torch.cuda.Stream()
+    for _ in range(max(3, args.warmup)):
+        rm.rmat_generate(t, 34, 0, chunk, out, s)
+    s.synchronize()
+    with ClockSampler(0) as clocks:
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        for c in range(nchunks):
+            rm.rmat_generate(t, 34, c * chunk, chunk, out, s)
+        b.record(s)
+        s.synchronize()
+    dt = a.elapsed_time(b) / 1e3
+    peak, src = measured_peak()
+    gbs = 16.0 * chunk * nchunks / dt / 1e9
+    print(json.dumps({"workload": "c3", "config": {"workload": "R-MAT k=34, m=2^35 streamed in 32 chunks of 2^30 "
+                      "edges into one 16 GiB buffer, u64 pairs, undirected, per-level noise +-0.05 on "
+                      "0.57,0.19,0.19,0.05", "ell": choice["ell"], "launch": list(shape)},
+                      "metric": "edges/s", "value": chunk * nchunks / dt, "seconds": dt,
+                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                                   "peak_source": src},
+                      "clocks": clocks.summary()}), flush=True)
+
+
+def run_c4(args):
+    """4096 graphs, k ~ U{10..24}, m = round(2^U(12,26)), parameters ~
+    Dirichlet(57,19,19,5): one persistent launch per wave (captured in a CUDA
+    graph) against one launch per graph."""
+    import torch
+    import paper_1905_03525_gb300 as rm
+    from paper_1905_03525_gb300 import autotune
+    from paper_1905_03525_gb300.workloads import batched_graphs
+    graphs = batched_graphs(args.graphs)
+    tables, choices = autotune.plan_batch(graphs)
+    budget = int(args.wave_gib * (1 << 30))
+    waves, cur, cur_b = [], [], 0
+    for i, g in enumerate(graphs):
+        nb = 8 * g["m"]
+        if cur and cur_b + nb > budget:
+            waves.append(cur)
+            cur, cur_b = [], 0
+        cur.append(i)
+        cur_b += (nb + 255) // 256 * 256
+    if cur:
+        waves.append(cur)
+    arena = torch.empty(budget // 4 + 64 * len(graphs), dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    t_batch = t_loop = t_loop_graph = 0.0
+    edges = 0
+    checked = 0
+    for w in waves:
+        outs, off = [], 0
+        for i in w:
+            n = 2 * graphs[i]["m"]
+            outs.append(arena[off:off + n].view(-1, 2))
+            off += (n + 63) // 64 * 64
+        b = rm.rmat_batch_create()
+        for i, o in zip(w, outs):
+            rm.rmat_batch_add(b, tables[i], graphs[i]["seed"], 0, graphs[i]["m"], o)
+        rm.rmat_batch_prepare(b)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            rm.rmat_batch_launch(b, s)
+        g.replay()
+        t_batch += _events_time(g.replay, s, 3)
+        # reference bytes for a few graphs of the wave, then the per-graph loop
+        probe = [0, len(w) // 2, len(w) - 1]
+        saved = [outs[j].clone() for j in probe]
+        def loop():
+            for i, o in zip(w, outs):
+                rm.rmat_generate(tables[i], graphs[i]["seed"], 0, graphs[i]["m"], o, s)
+        loop()
+        t_loop += _events_time(loop, s, 2)
+        gl = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gl, stream=s):
+            loop()
+        gl.replay()
+        t_loop_graph += _events_time(gl.replay, s, 2)
+        for j, ref in zip(probe, saved):
+            assert torch.equal(outs[j], ref), "batched and per-graph bytes differ"
+            checked += 1
+        edges += sum(graphs[i]["m"] for i in w)
+        b.free()
+        del g, gl
+    print(json.dumps({"workload": "c4", "config": {"workload": f"{len(graphs)} graphs, k~U{{10..24}}, "
+                      "m=round(2^U(12,26)), (a,b,c,d)~Dirichlet(57,19,19,5), seed=4096+i, u32",
+                      "waves": len(waves), "wave_budget_gib": args.wave_gib,
+                      "table_choice_per_k": {str(k): v for k, v in sorted(choices.items())}},
+                      "metric": "edges/s", "edges": edges,
+                      "batched_edges_per_s": edges / t_batch, "per_graph_eager_edges_per_s": edges / t_loop,
+                      "per_graph_cuda_graph_edges_per_s": edges / t_loop_graph,
+                      "speedup_vs_eager": t_loop / t_batch, "speedup_vs_graphed_loop": t_loop_graph / t_batch,
+                      "graphs_checked_bytewise": checked}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c1":
+        run_c1(args)
+    elif args.workload == "c3":
+        run_c3(args)
+    elif args.workload == "c4":
+        run_c4(args)
+    elif args.workload == "c5":
+        from paper_1905_03525_gb300 import serve
+        serve.bench(args)
     else:
         run_ours(args)
 

@@ -219,6 +219,83 @@ rmat_status rmat_batch_size(const rmat_batch *b, uint64_t *graphs, uint64_t *edg
 void rmat_batch_free(rmat_batch *b);
 
 /* ---------------------------------------------------------------------- */
+/* Serving: continuous batching of generation requests                     */
+/* ---------------------------------------------------------------------- */
+/* A server owns one device-memory arena (hbm_budget_bytes) and one worker
+ * thread.  Requests queue in FIFO order and are admitted when a slot is free
+ * and their table plus one chunk buffer fit the arena.  Each step generates
+ * the next chunk of admitted requests in one persistent batched launch --
+ * requests that finish with this chunk first, then the others round-robin, up
+ * to step_edges edges -- and consumes the chunks: a checksum kernel adds
+ * mix(e, row, col) of every edge into the request's checksum (see
+ * rmat_request_status_t), and an optional callback sees each chunk on the
+ * device.  A finished request frees its memory and slot before the next step,
+ * so queued requests join while others are still running.  Each request's
+ * edges (and checksum) are identical to rmat_generate of the same table and
+ * seed, alone or in any mix.  Arrival, admission and completion times are on
+ * the server's clock (seconds since create). */
+typedef struct rmat_server rmat_server; /* opaque */
+
+typedef struct {
+    uint64_t hbm_budget_bytes; /* device memory for tables and chunk buffers (allocated at create) */
+    uint64_t chunk_edges;      /* largest chunk of one request per step (e.g. 2^28) */
+    uint64_t step_edges;       /* edges per step over all requests (>= chunk_edges) */
+    int max_active;            /* requests generated concurrently, 1..4096 */
+    double wait_timeout_s;     /* host-side bound on one step; beyond it the step's requests fail */
+} rmat_server_config_t;
+
+typedef struct {
+    double a, b, c, d;    /* as rmat_build_table */
+    int k;
+    uint64_t m;           /* edges 0..m-1 of the graph, m >= 1 */
+    uint64_t seed;
+    uint64_t table_bound; /* variable-length table bound; 0 = 4096 */
+    unsigned flags;       /* RMAT_UNDIRECTED or 0 */
+} rmat_request_t;
+
+enum { RMAT_REQ_QUEUED = 0, RMAT_REQ_RUNNING = 1, RMAT_REQ_DONE = 2, RMAT_REQ_FAILED = 3 };
+
+typedef struct {
+    uint64_t id;
+    int state;            /* RMAT_REQ_* */
+    uint64_t edges_done;
+    /* sum mod 2^64 over the request's edges e of mix(x), with
+     *   x = e*0x9E3779B97F4A7C15 + row*0xC2B2AE3D27D4EB4F + col*0x165667B19E3779F9
+     * and mix the splitmix64 finaliser (x ^= x>>30; x *= 0xBF58476D1CE4E5B9;
+     * x ^= x>>27; x *= 0x94D049BB133111EB; x ^= x>>31), all mod 2^64 */
+    uint64_t checksum;
+    double submit_s, admit_s, done_s;
+    rmat_status error;    /* why the request failed, if it did */
+} rmat_request_status_t;
+
+typedef struct {
+    uint64_t steps, edges, queued, active, memory_used;
+    double clock_s;
+} rmat_server_stats_t;
+
+/* Called on the worker thread after each chunk is generated and checksummed;
+ * device_edges (on the server's device) is valid only during the call. */
+typedef void (*rmat_chunk_fn)(void *user, uint64_t request_id, uint64_t edge_offset, uint64_t count,
+                              const void *device_edges);
+
+/* Create a server on the current device; allocates the arena and starts the
+ * worker. */
+rmat_status rmat_server_create(const rmat_server_config_t *cfg, rmat_server **out);
+rmat_status rmat_server_set_chunk_callback(rmat_server *s, rmat_chunk_fn fn, void *user);
+/* Build the request's table on the calling thread and queue it.  Thread-safe.
+ * RMAT_ERR_OUT_OF_MEMORY if the request could never fit the budget. */
+rmat_status rmat_server_submit(rmat_server *s, const rmat_request_t *req, uint64_t *id);
+rmat_status rmat_server_status(rmat_server *s, uint64_t id, rmat_request_status_t *st);
+/* Block until the request is done or failed, or timeout_s passes
+ * (RMAT_ERR_TIMEOUT; the request keeps running). */
+rmat_status rmat_server_wait(rmat_server *s, uint64_t id, double timeout_s, rmat_request_status_t *st);
+/* Block until every submitted request is done or failed. */
+rmat_status rmat_server_drain(rmat_server *s, double timeout_s);
+rmat_status rmat_server_stats(rmat_server *s, rmat_server_stats_t *out);
+/* Fail the requests still queued, finish the running ones, free everything. */
+void rmat_server_destroy(rmat_server *s);
+
+/* ---------------------------------------------------------------------- */
 /* Generation without device allocation                                    */
 /* ---------------------------------------------------------------------- */
 /* The paper has no counterpart to this call; it serves callers that cannot

@@ -36,6 +36,32 @@ class TableInfo(ctypes.Structure):
                 ("flags", ctypes.c_uint), ("device_image_bytes", ctypes.c_uint64)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("chunk_edges", ctypes.c_uint64),
+                ("step_edges", ctypes.c_uint64), ("max_active", ctypes.c_int), ("wait_timeout_s", ctypes.c_double)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("b", ctypes.c_double), ("c", ctypes.c_double), ("d", ctypes.c_double),
+                ("k", ctypes.c_int), ("m", ctypes.c_uint64), ("seed", ctypes.c_uint64),
+                ("table_bound", ctypes.c_uint64), ("flags", ctypes.c_uint)]
+
+
+class RequestStatus(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("state", ctypes.c_int), ("edges_done", ctypes.c_uint64),
+                ("checksum", ctypes.c_uint64), ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
+                ("done_s", ctypes.c_double), ("error", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_uint64), ("edges", ctypes.c_uint64), ("queued", ctypes.c_uint64),
+                ("active", ctypes.c_uint64), ("memory_used", ctypes.c_uint64), ("clock_s", ctypes.c_double)]
+
+
+CHUNK_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                            ctypes.c_void_p)
+
+
 class LaunchConfig(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("tile_edges", ctypes.c_int)]
 
@@ -67,6 +93,14 @@ SIGNATURES = [
     ("rmat_batch_launch", _st, [_vp, _vp]),
     ("rmat_batch_size", _st, [_vp, _vp, _vp]),
     ("rmat_batch_free", None, [_vp]),
+    ("rmat_server_create", _st, [_vp, _vp]),
+    ("rmat_server_set_chunk_callback", _st, [_vp, _vp, _vp]),
+    ("rmat_server_submit", _st, [_vp, _vp, _vp]),
+    ("rmat_server_status", _st, [_vp, _u64, _vp]),
+    ("rmat_server_wait", _st, [_vp, _u64, _dbl, _vp]),
+    ("rmat_server_drain", _st, [_vp, _dbl]),
+    ("rmat_server_stats", _st, [_vp, _vp]),
+    ("rmat_server_destroy", None, [_vp]),
     ("rmat_generate_batch_noalloc", _st, [_vp, _vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
     ("rmat_check_device_errors", _st, []),
     ("rmat_version", ctypes.c_char_p, []),

@@ -1,0 +1,199 @@
+"""Autotuner: picks the table (variable-length bound or fixed path length l),
+the per-level group length l, and the launch shape (threads per CTA, CTAs per
+SM, edges per warp tile) by timing real launches on the current GPU.
+
+The paper tunes the table size by hand per machine (Fig. 1: throughput
+against table size; the best size tracks the cache hierarchy).  On GB300 the
+table lives in shared memory, so the trade-off is levels per draw (larger
+tables) against shared-memory footprint and staging cost; the tuner measures
+it instead of modelling it.  Results are cached per device in a JSON file
+(``$RMAT_TUNE_CACHE`` or ``~/.cache/rmat_gb300/``).
+
+Everything here sits above the C ABI: it only builds tables, sets launch
+shapes and times ``rmat_generate`` / ``rmat_batch_launch`` with CUDA events.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import threading
+
+import numpy as np
+
+from . import (rmat_batch_add, rmat_batch_create, rmat_batch_launch, rmat_batch_prepare, rmat_build_table,
+               rmat_build_table_fixed, rmat_build_table_levels, rmat_generate, rmat_set_launch_config,
+               rmat_table_info, empty_edges)
+
+LAUNCH_SHAPES = [(1024, 1, 256), (1024, 1, 512), (768, 1, 256), (512, 2, 256), (512, 1, 512), (256, 4, 256)]
+BOUNDS = [1 << b for b in range(8, 15)]
+ELLS = [4, 5, 6, 7, 8]
+_lock = threading.Lock()
+
+
+def _cache_path() -> str:
+    base = os.environ.get("RMAT_TUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache", "rmat_gb300")
+    os.makedirs(base, exist_ok=True)
+    import torch
+    name = torch.cuda.get_device_name().replace(" ", "_")
+    return os.path.join(base, f"tune_{name}.json")
+
+
+def _load() -> dict:
+    try:
+        with open(_cache_path()) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _store(key: str, value) -> None:
+    with _lock:
+        d = _load()
+        d[key] = value
+        tmp = _cache_path() + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(d, f, indent=1, sort_keys=True)
+        os.replace(tmp, _cache_path())
+
+
+def time_launches(fn, reps: int = 3, warmup: int = 1) -> float:
+    """Mean device time (s) of fn(stream) over `reps` back-to-back launches."""
+    import torch
+    s = torch.cuda.Stream()
+    for _ in range(warmup):
+        fn(s)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    for _ in range(reps):
+        fn(s)
+    b.record(s)
+    s.synchronize()
+    return a.elapsed_time(b) / 1e3 / reps
+
+
+def tune_launch(table, sample_edges: int = 1 << 26, shapes=LAUNCH_SHAPES, out=None, seed: int = 1):
+    """Time `table` under each launch shape, keep the fastest (applied to the
+    table with rmat_set_launch_config) and return (shape, edges_per_s)."""
+    info = rmat_table_info(table)
+    key = (f"launch:k{info['k']}:e{info['entries']}:b{info['bits']}:l{info['max_len']}:g{info['groups']}:"
+           f"u{info['index_bytes']}:f{info['flags']}")
+    cached = _load().get(key)
+    if cached:
+        rmat_set_launch_config(table, *cached["shape"])
+        return tuple(cached["shape"]), cached["edges_per_s"]
+    if out is None:
+        out = empty_edges(sample_edges, info["k"])
+    best = None
+    for shape in shapes:
+        rmat_set_launch_config(table, *shape)
+        dt = time_launches(lambda s: rmat_generate(table, seed, 0, sample_edges, out, s))
+        rate = sample_edges / dt
+        if best is None or rate > best[1]:
+            best = (shape, rate)
+    rmat_set_launch_config(table, *best[0])
+    _store(key, {"shape": list(best[0]), "edges_per_s": best[1]})
+    return best
+
+
+def _param_key(abcd) -> str:
+    return ",".join(f"{x:.3f}" for x in abcd)
+
+
+def tune_table(k: int, abcd, sample_edges: int = 1 << 24, bounds=BOUNDS, ells=ELLS, seed: int = 1):
+    """Fastest table for (k, a, b, c, d): a variable-length table with one of
+    `bounds`, or a fixed-length table with one of `ells`.  Returns a dict
+    {"kind": "variable"|"fixed", "bound"|"ell": ..., "edges_per_s": ...}."""
+    key = f"table:k{k}:p{_param_key(abcd)}"
+    cached = _load().get(key)
+    if cached:
+        return cached
+    out = empty_edges(sample_edges, k)
+    cands = [("variable", b) for b in bounds] + [("fixed", l) for l in ells if l <= k]
+    best = None
+    for kind, x in cands:
+        t = rmat_build_table(*abcd, k, x) if kind == "variable" else rmat_build_table_fixed(*abcd, k, x)
+        if rmat_table_info(t)["device_image_bytes"] > 160 * 1024:
+            continue  # would not fit shared memory beside the warp tiles
+        dt = time_launches(lambda s: rmat_generate(t, seed, 0, sample_edges, out, s))
+        rate = sample_edges / dt
+        if best is None or rate > best["edges_per_s"]:
+            best = {"kind": kind, ("bound" if kind == "variable" else "ell"): x, "edges_per_s": rate}
+    _store(key, best)
+    return best
+
+
+def tune_levels(k: int, P_levels, flags: int = 0, sample_edges: int = 1 << 24, ells=(3, 4, 5, 6, 7), seed: int = 1):
+    """Fastest group length l for a per-level table (one table per l levels)."""
+    P = np.asarray(P_levels, np.float64).reshape(-1, 4)
+    key = f"levels:k{k}:f{flags}:p{_param_key(P.mean(axis=0))}"
+    cached = _load().get(key)
+    if cached:
+        return cached
+    out = empty_edges(sample_edges, k)
+    best = None
+    for ell in ells:
+        if (k + ell - 1) // ell > 64:
+            continue
+        t = rmat_build_table_levels(P, k, ell, flags)
+        if rmat_table_info(t)["device_image_bytes"] > 160 * 1024:
+            continue
+        dt = time_launches(lambda s: rmat_generate(t, seed, 0, sample_edges, out, s))
+        rate = sample_edges / dt
+        if best is None or rate > best["edges_per_s"]:
+            best = {"ell": ell, "edges_per_s": rate}
+    _store(key, best)
+    return best
+
+
+def build_tuned_table(k: int, abcd, m: int | None = None, choice=None):
+    """Build the table the tuner picked for (k, params).  For a graph of m
+    edges the table's blob is also kept below 1/8 of the graph's output bytes
+    (staging a table costs about its own size in traffic per CTA)."""
+    choice = choice or tune_table(k, abcd)
+    if choice["kind"] == "fixed":
+        ell = min(choice["ell"], k)
+        if m is not None:
+            while ell > 2 and 8 * 4 ** ell > m:   # table bytes <= 1/8 of the output bytes
+                ell -= 1
+        return rmat_build_table_fixed(*abcd, k, ell)
+    bound = choice["bound"]
+    if m is not None:
+        while bound > 64 and 8 * bound > m:
+            bound //= 2
+    return rmat_build_table(*abcd, k, bound)
+
+
+def plan_batch(graphs, representative=None, sample_edges: int = 1 << 22):
+    """Table choice for every graph of a batch: the tuner runs once per k on
+    representative parameters (default: the mean of the graphs' parameters),
+    then each graph gets a table of that kind sized for its edge count.
+    Returns a list of tables."""
+    P = np.asarray([g["abcd"] for g in graphs], np.float64)
+    rep = tuple(float(x) for x in (representative if representative is not None else P.mean(axis=0)))
+    rep = tuple(x / sum(rep) for x in rep)
+    choices = {}
+    tables = []
+    for g in graphs:
+        k = g["k"]
+        if k not in choices:
+            choices[k] = tune_table(k, rep, sample_edges=sample_edges)
+        tables.append(build_tuned_table(k, g["abcd"], g["m"], choices[k]))
+    return tables, choices
+
+
+def tune_batch_shape(tables, counts, seeds, outs, shapes=((1024, 1, 256), (1024, 1, 128), (512, 2, 256),
+                                                          (512, 2, 128), (768, 1, 256))):
+    """Fastest launch shape of the batched kernel for this batch."""
+    best = None
+    for shape in shapes:
+        b = rmat_batch_create()
+        for t, m, s, o in zip(tables, counts, seeds, outs):
+            rmat_batch_add(b, t, s, 0, m, o)
+        rmat_batch_prepare(b, *shape)
+        dt = time_launches(lambda s_: rmat_batch_launch(b, s_), reps=2)
+        if best is None or dt < best[1]:
+            best = (shape, dt)
+        b.free()
+    return best

@@ -415,6 +415,49 @@ __global__ void __launch_bounds__(1024) k_batch(BatchArgs B) {
     if (lane == 0 && W.issued) dev::bulk_wait_all();
 }
 
+// Order-independent checksum of the edges of every job of a step: the sum
+// mod 2^64 of mix(e, row, col) over the job's edges, where
+//   x = e * 0x9E3779B97F4A7C15 + row * 0xC2B2AE3D27D4EB4F + col * 0x165667B19E3779F9
+//   mix = x ^ (x >> 30); * 0xBF58476D1CE4E5B9; ^ (>> 27); * 0x94D049BB133111EB; ^ (>> 31)
+// (splitmix64's finaliser).  Chunk sums add up to the graph's sum however the
+// graph is split.  sums[j] accumulates job j's sum.
+template <bool U64>
+__global__ void __launch_bounds__(256) k_checksum(BatchArgs B, unsigned long long *sums) {
+    __shared__ unsigned long long part[8];
+    for (uint64_t unit = blockIdx.x; unit < B.units; unit += gridDim.x) {
+        const uint32_t jid = B.unit_job[unit];
+        const Job &J = B.jobs[jid];
+        const uint64_t f0 = (unit - J.unit_begin) * B.unit_edges;
+        const uint64_t end = min(J.count, f0 + B.unit_edges);
+        unsigned long long acc = 0;
+        for (uint64_t i = f0 + threadIdx.x; i < end; i += blockDim.x) {
+            uint64_t r, c;
+            if (U64) {
+                const ulonglong2 v = reinterpret_cast<const ulonglong2 *>(J.out)[i];
+                r = v.x;
+                c = v.y;
+            } else {
+                const uint2 v = reinterpret_cast<const uint2 *>(J.out)[i];
+                r = v.x;
+                c = v.y;
+            }
+            uint64_t x = (J.e0 + i) * 0x9E3779B97F4A7C15ull + r * 0xC2B2AE3D27D4EB4Full + c * 0x165667B19E3779F9ull;
+            x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+            x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+            acc += x ^ (x >> 31);
+        }
+        for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long tot = 0;
+            for (int w = 0; w < int(blockDim.x >> 5); ++w) tot += part[w];
+            atomicAdd(sums + jid, tot);
+        }
+        __syncthreads();
+    }
+}
+
 struct NaiveArgs {
     int k;
     unsigned flags;
@@ -641,6 +684,17 @@ rmat_status launch_batch(bool u64, const BatchArgs &args, int grid, int threads,
     void *params[] = {&a};
     e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), params, smem, stream);
     if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return RMAT_OK;
+}
+
+rmat_status launch_checksum(bool u64, const BatchArgs &args, unsigned long long *sums, int grid,
+                            cudaStream_t stream) {
+    void *fn = u64 ? reinterpret_cast<void *>(&k_checksum<true>) : reinterpret_cast<void *>(&k_checksum<false>);
+    BatchArgs a = args;
+    void *params[] = {&a, &sums};
+    const unsigned g = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(uint64_t(grid), args.units)));
+    cudaError_t e = cudaLaunchKernel(fn, dim3(g), dim3(256), params, 0, stream);
+    if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("checksum launch: ") + cudaGetErrorString(e));
     return RMAT_OK;
 }
 

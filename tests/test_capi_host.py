@@ -153,3 +153,12 @@ def test_launch_config_roundtrip_and_checks():
         rm.rmat_set_launch_config(t, 100, 1, 128)
     with pytest.raises(rm.RmatError):
         rm.rmat_set_launch_config(t, 256, 1, 40)
+
+
+def test_server_create_fails_cleanly_without_a_device():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    from paper_1905_03525_gb300.serve import Server
+    with pytest.raises(rm.RmatError):
+        Server(1 << 30)

@@ -328,8 +328,9 @@ def run_c1(args):
     with torch.cuda.graph(g, stream=s):
         for _ in range(20):
             rm.rmat_generate(t, 1, 0, m, out, s)
-    g.replay()
-    dtg = _events_time(g.replay, s, 5) / 20
+    with torch.cuda.stream(s):
+        g.replay()
+        dtg = _events_time(g.replay, s, 5) / 20
     print(json.dumps({"workload": "c1", "config": {"workload": "R-MAT k=16, m=2^20, fixed l=4 (256 entries), "
                       "a,b,c,d=0.57,0.19,0.19,0.05, seed=1, u32"}, "metric": "edges/s", "value": m / dt,
                       "ms_per_launch": dt * 1e3, "graph_replay_edges_per_s": m / dtg,
@@ -412,8 +413,9 @@ def run_c4(args):
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=s):
             rm.rmat_batch_launch(b, s)
-        g.replay()
-        t_batch += _events_time(g.replay, s, 3)
+        with torch.cuda.stream(s):
+            g.replay()
+            t_batch += _events_time(g.replay, s, 3)
         # reference bytes for a few graphs of the wave, then the per-graph loop
         probe = [0, len(w) // 2, len(w) - 1]
         saved = [outs[j].clone() for j in probe]
@@ -425,8 +427,9 @@ def run_c4(args):
         gl = torch.cuda.CUDAGraph()
         with torch.cuda.graph(gl, stream=s):
             loop()
-        gl.replay()
-        t_loop_graph += _events_time(gl.replay, s, 2)
+        with torch.cuda.stream(s):
+            gl.replay()
+            t_loop_graph += _events_time(gl.replay, s, 2)
         for j, ref in zip(probe, saved):
             assert torch.equal(outs[j], ref), "batched and per-graph bytes differ"
             checked += 1

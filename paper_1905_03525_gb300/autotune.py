@@ -101,11 +101,14 @@ def _param_key(abcd) -> str:
     return ",".join(f"{x:.3f}" for x in abcd)
 
 
-def tune_table(k: int, abcd, sample_edges: int = 1 << 24, bounds=BOUNDS, ells=ELLS, seed: int = 1):
+def tune_table(k: int, abcd, sample_edges: int = 1 << 24, bounds=BOUNDS, ells=ELLS, seed: int = 1,
+               max_blob_bytes: int = 160 * 1024):
     """Fastest table for (k, a, b, c, d): a variable-length table with one of
-    `bounds`, or a fixed-length table with one of `ells`.  Returns a dict
-    {"kind": "variable"|"fixed", "bound"|"ell": ..., "edges_per_s": ...}."""
-    key = f"table:k{k}:p{_param_key(abcd)}"
+    `bounds`, or a fixed-length table with one of `ells`, among those whose
+    device blob is at most `max_blob_bytes` (what the launch can stage in
+    shared memory).  Returns a dict {"kind": "variable"|"fixed",
+    "bound"|"ell": ..., "edges_per_s": ...}."""
+    key = f"table:k{k}:p{_param_key(abcd)}:s{max_blob_bytes}"
     cached = _load().get(key)
     if cached:
         return cached
@@ -114,7 +117,7 @@ def tune_table(k: int, abcd, sample_edges: int = 1 << 24, bounds=BOUNDS, ells=EL
     best = None
     for kind, x in cands:
         t = rmat_build_table(*abcd, k, x) if kind == "variable" else rmat_build_table_fixed(*abcd, k, x)
-        if rmat_table_info(t)["device_image_bytes"] > 160 * 1024:
+        if rmat_table_info(t)["device_image_bytes"] > max_blob_bytes:
             continue  # would not fit shared memory beside the warp tiles
         dt = time_launches(lambda s: rmat_generate(t, seed, 0, sample_edges, out, s))
         rate = sample_edges / dt
@@ -165,11 +168,20 @@ def build_tuned_table(k: int, abcd, m: int | None = None, choice=None):
     return rmat_build_table(*abcd, k, bound)
 
 
+def batch_blob_budget(threads: int = 1024, tile: int = 256, u64: bool = False) -> int:
+    """Shared memory the batched kernel has left for a staged table blob."""
+    import torch
+    smem = torch.cuda.get_device_properties(torch.cuda.current_device()).shared_memory_per_block_optin
+    per_warp = 2 * tile * (16 if u64 else 8) + 3 * tile
+    return smem - 16 - (threads // 32) * per_warp
+
+
 def plan_batch(graphs, representative=None, sample_edges: int = 1 << 22):
     """Table choice for every graph of a batch: the tuner runs once per k on
     representative parameters (default: the mean of the graphs' parameters),
-    then each graph gets a table of that kind sized for its edge count.
-    Returns a list of tables."""
+    among tables that the batched kernel can stage in shared memory, then each
+    graph gets a table of that kind sized for its edge count.  Returns the
+    tables and the per-k choices."""
     P = np.asarray([g["abcd"] for g in graphs], np.float64)
     rep = tuple(float(x) for x in (representative if representative is not None else P.mean(axis=0)))
     rep = tuple(x / sum(rep) for x in rep)
@@ -178,7 +190,7 @@ def plan_batch(graphs, representative=None, sample_edges: int = 1 << 22):
     for g in graphs:
         k = g["k"]
         if k not in choices:
-            choices[k] = tune_table(k, rep, sample_edges=sample_edges)
+            choices[k] = tune_table(k, rep, sample_edges=sample_edges, max_blob_bytes=batch_blob_budget())
         tables.append(build_tuned_table(k, g["abcd"], g["m"], choices[k]))
     return tables, choices
 

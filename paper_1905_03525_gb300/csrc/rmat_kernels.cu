@@ -525,9 +525,26 @@ unsigned *device_error_ptr() {
     return static_cast<unsigned *>(p);
 }
 
-cudaError_t set_smem_attr(void *kernel, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+// The dynamic shared-memory limit is an attribute of the kernel function, not
+// of a launch: raise it once per kernel to the device maximum, so that any
+// later launch of that kernel may use up to the maximum.  (Occupancy still
+// follows each launch's actual size.)
+std::mutex g_attr_mu;
+std::vector<std::pair<void *, int>> g_attr_done;  // (kernel, device)
+
+cudaError_t set_smem_attr(void *kernel, size_t /*bytes*/) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    for (const auto &kd : g_attr_done)
+        if (kd.first == kernel && kd.second == dev) return cudaSuccess;
+    int max_smem = 0;
+    e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e == cudaSuccess) g_attr_done.emplace_back(kernel, dev);
+    return e;
 }
 
 }  // namespace

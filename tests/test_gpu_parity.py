@@ -227,3 +227,18 @@ def test_k34_per_level_chunk_full_size():
     assert bool((out[:, 0] <= out[:, 1]).all())
     del out
     torch.cuda.empty_cache()
+
+
+def test_tables_with_different_shared_memory_needs_interleave():
+    """Launch plans are cached per table; the kernel's shared-memory limit is
+    per function.  Alternating a large and a small table of the same kernel
+    must keep working (and stay exact)."""
+    k, m = 26, 70_000
+    big = rm.rmat_build_table(*G500, k, 1 << 14)    # ~129 KiB blob, smaller tiles
+    small = rm.rmat_build_table(*G500, k, 256)
+    refs = {}
+    for name, t, bound in [("big", big, 1 << 14), ("small", small, 256), ("big", big, 1 << 14), ("small", small, 256)]:
+        got = gpu_edges(t, k, 9, 0, m)
+        if name not in refs:
+            refs[name] = oracle.generate([oracle.Table.variable(*G500, k, bound)], k, 9, 0, m)
+        assert_same(got, refs[name])

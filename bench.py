@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--cpu-sample-edges", type=int, default=1 << 27)
     ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5"], default="c2",
                     help="c2 (default): the contract line; c1/c3/c4/c5: the other configurations, one JSON line each")
+    ap.add_argument("--log2m", type=int, default=LOG2M,
+                    help="c2: edges per GPU = 2^log2m (default 30; smaller only for profiling captures)")
     ap.add_argument("--graphs", type=int, default=4096, help="c4: number of graphs")
     ap.add_argument("--wave-gib", type=float, default=48.0, help="c4: output budget per batched launch")
     ap.add_argument("--requests", type=int, default=256, help="c5: trace length")
@@ -197,8 +199,8 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    m = 1 << LOG2M
-    e0 = rank * m
+    from paper_1905_03525_gb300.sharding import weak_range
+    e0, m = weak_range(rank, 1 << args.log2m)
     table = rm.rmat_build_table(*G500, K, BOUND)
     rm.rmat_table_upload(table)
     out = rm.empty_edges(m, K)

@@ -69,6 +69,46 @@ __device__ __forceinline__ uint32_t lds32(uint32_t addr) {
     return v;
 }
 
+__device__ __forceinline__ uint32_t lds8(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t lds16(uint32_t addr) {
+    unsigned short v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ uint2 lds64(uint32_t addr) {
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ ulonglong2 lds128u64(uint32_t addr) {
+    ulonglong2 v;
+    asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ void sts8(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared.u8 [%0], %1;" ::"r"(addr), "h"((unsigned short)v) : "memory");
+}
+
+__device__ __forceinline__ void sts16(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared.u16 [%0], %1;" ::"r"(addr), "h"((unsigned short)v) : "memory");
+}
+
+__device__ __forceinline__ void sts64(uint32_t addr, uint32_t a, uint32_t b) {
+    asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
+}
+
+__device__ __forceinline__ void sts128u64(uint32_t addr, uint64_t a, uint64_t b) {
+    asm volatile("st.shared.v2.u64 [%0], {%1, %2};" ::"r"(addr), "l"(a), "l"(b) : "memory");
+}
+
 __device__ __forceinline__ uint4 lds128(uint32_t addr) {
     uint4 v;
     asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
@@ -80,22 +120,9 @@ __device__ __forceinline__ uint4 lds128(uint32_t addr) {
 // Where one table (group) lives and how to split a word for it.
 template <bool SMEM>
 struct Group {
-    uint32_t sA, sB;             // shared byte addresses of A and B (SMEM)
-    const uint32_t *gA, *gB;     // global addresses (!SMEM)
-    uint32_t mulb, mask;         // 2^b, 2^b - 1
-
-    __device__ __forceinline__ uint32_t a(uint32_t j) const {
-        if constexpr (SMEM) return lds32(sA + 4u * j);
-        else return __ldg(gA + j);
-    }
-    __device__ __forceinline__ uint32_t b32(uint32_t i) const {
-        if constexpr (SMEM) return lds32(sB + 4u * i);
-        else return __ldg(gB + i);
-    }
-    __device__ __forceinline__ uint4 b128(uint32_t i) const {
-        if constexpr (SMEM) return lds128(sB + 16u * i);
-        else return __ldg(reinterpret_cast<const uint4 *>(gB) + i);
-    }
+    uint32_t sA, sBs, sBa;            // shared byte addresses (SMEM)
+    const uint32_t *gA, *gBs, *gBa;   // global addresses (!SMEM)
+    uint32_t mulb;                    // 2^b: column j = umulhi(u, 2^b)
 };
 
 // Blob header word `w` (group descriptors), from shared or global memory.
@@ -109,14 +136,16 @@ template <bool SMEM>
 __device__ __forceinline__ Group<SMEM> group(uint32_t sbase, const uint32_t *gblob, uint32_t g) {
     Group<SMEM> G;
     const uint32_t aoff = blob_word<SMEM>(sbase, gblob, g);
-    const uint32_t boff = blob_word<SMEM>(sbase, gblob, 64u + g);
-    const uint32_t bits = blob_word<SMEM>(sbase, gblob, 128u + g);
+    const uint32_t bsoff = blob_word<SMEM>(sbase, gblob, 64u + g);
+    const uint32_t baoff = blob_word<SMEM>(sbase, gblob, 128u + g);
+    const uint32_t bits = blob_word<SMEM>(sbase, gblob, 192u + g);
     G.sA = sbase + 4u * aoff;
-    G.sB = sbase + 4u * boff;
+    G.sBs = sbase + 4u * bsoff;
+    G.sBa = sbase + 4u * baoff;
     G.gA = gblob + aoff;
-    G.gB = gblob + boff;
+    G.gBs = gblob + bsoff;
+    G.gBa = gblob + baoff;
     G.mulb = 1u << bits;
-    G.mask = G.mulb - 1u;
     return G;
 }
 
@@ -150,26 +179,34 @@ struct Acc64 {
     __device__ __forceinline__ uint64_t out_col(int k) const { return col >> (64 - k); }
 };
 
-// One alias draw from word u, appended to acc.
-//   column j = top b bits of u, residual r = the low 32-b bits; one 32x32->64
-//   multiply u * 2^b + (2^b - 1) yields j in the high word and
-//   (r << b) | (2^b - 1) in the low word, and with A[j] = (thr[j] << b) |
-//   alias[j] the draw keeps j iff that low word < A[j]  (<=> r < thr[j]).
+// One alias draw from word u, appended to acc: column j = top b bits of u
+// (the high word of u * 2^b); the draw keeps j iff u < A[j] =
+// (j << (32-b)) + thr[j], i.e. iff the residual (low 32-b bits) < thr[j],
+// and then appends path Bs[j], else path Ba[j] (the alias's).
 // Compact path entry x: row bits in 31..19, length in 18..13, column bits in
 // 12..0 (both left-aligned in their 13-bit fields).
 template <int FMT, bool SMEM, class Acc>
 __device__ __forceinline__ void draw(const Group<SMEM> &G, uint32_t u, Acc &acc) {
-    const uint64_t t = uint64_t(u) * G.mulb + G.mask;
-    const uint32_t j = uint32_t(t >> 32);
-    const uint32_t rs = uint32_t(t);
-    const uint32_t a = G.a(j);
-    const uint32_t sel = rs < a ? j : (a & G.mask);
-    if constexpr (FMT == 0) {
-        const uint32_t x = G.b32(sel);
-        acc.append(x & 0xFFF80000u, x << 19, (x >> 13) & 63u);
+    const uint32_t j = __umulhi(u, G.mulb);
+    if constexpr (SMEM) {
+        const uint32_t off = 4u * j;
+        const bool keep = u < lds32(G.sA + off);
+        if constexpr (FMT == 0) {
+            const uint32_t x = lds32((keep ? G.sBs : G.sBa) + off);
+            acc.append(x & 0xFFF80000u, x << 19, (x >> 13) & 63u);
+        } else {
+            const uint4 v = lds128((keep ? G.sBs : G.sBa) + 4u * off);
+            acc.append(v.x, v.y, v.z);
+        }
     } else {
-        const uint4 v = G.b128(sel);
-        acc.append(v.x, v.y, v.z);
+        const bool keep = u < __ldg(G.gA + j);
+        if constexpr (FMT == 0) {
+            const uint32_t x = __ldg((keep ? G.gBs : G.gBa) + j);
+            acc.append(x & 0xFFF80000u, x << 19, (x >> 13) & 63u);
+        } else {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(keep ? G.gBs : G.gBa) + j);
+            acc.append(v.x, v.y, v.z);
+        }
     }
 }
 
@@ -227,6 +264,11 @@ __device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src, uint32
 __device__ __forceinline__ void bulk_s2g(void *dst, const void *src_smem, uint32_t bytes) {
     asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
                  "r"(smem_u32(src_smem)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_s2g_addr(void *dst, uint32_t src_smem, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src_smem), "r"(bytes)
                  : "memory");
 }
 

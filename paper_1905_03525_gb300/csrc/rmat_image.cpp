@@ -1,24 +1,28 @@
 // rmat_image.cpp -- packing of the alias tables into the device image that the
 // sampling kernels stage into shared memory.
 //
-// Per table (group) of N = 2^b columns the image holds two arrays:
-//   A[j]  u32  (thr[j] << b) | alias[j]      -- one word decides a draw:
-//              with the word u = (j << (32-b)) | r, the draw keeps column j iff
-//              r < thr[j]  <=>  ((u << b) | (2^b - 1)) < A[j].
-//   B[i]       the path of entry i, ready to be OR-ed into left-aligned
-//              row/column accumulators:
+// Per table (group) of N = 2^b columns the image holds three arrays:
+//   A[j]   u32  (j << (32-b)) + thr[j]: the draw with 32-bit word u keeps
+//               column j = u >> (32-b) iff u < A[j]  (<=> residual < thr[j]);
+//   Bs[j]       the path of entry j          (taken when u < A[j]);
+//   Ba[j]       the path of entry alias[j]   (taken otherwise).
+// Holding the alias's path beside the column makes a draw two independent-of-
+// content loads: A[j], then Bs[j] or Ba[j] -- the same shared-memory traffic
+// as looking up alias[j] and then its path, with fewer instructions (no alias
+// index to extract, no second address from loaded data).
+// Path entries, ready to be OR-ed into left-aligned row/column accumulators:
 //     compact (paths <= 13 levels), u32:
 //              bits 31..19 row bits, left-aligned in the 13-bit field
 //              bits 18..13 path length L
 //              bits 12..0  column bits, left-aligned in the 13-bit field
 //     wide (paths <= 32 levels), uint4:
 //              {row bits << (32-L), column bits << (32-L), L, 0}
-// Two 4-byte shared-memory loads per draw (A[j], then B[sel]) is the least
-// shared-memory traffic for a random column: each costs one bank access per
-// lane.  The blob starts with a header of kHeaderWords words -- word g, 64+g
-// and 128+g hold the A offset, B offset and b of group g (offsets in words
-// from the blob start) -- followed by the groups back to back, each array
-// 16-byte aligned, so that one bulk copy stages descriptors and tables.
+// Two 4-byte random shared-memory loads per draw is the least traffic for a
+// random column: each costs one bank access per lane.  The blob starts with a
+// header of kHeaderWords words -- words g, 64+g, 128+g and 192+g hold the A,
+// Bs and Ba offsets (in words from the blob start) and b of group g -- followed
+// by the groups back to back, each array 16-byte aligned, so that one bulk
+// copy stages descriptors and tables.
 #include <algorithm>
 
 #include "rmat_internal.h"
@@ -54,7 +58,9 @@ rmat_status build_image(rmat_table *t) {
         GroupDesc d;
         d.a_off_words = uint32_t(total);
         total += round16w(N);
-        d.b_off_words = uint32_t(total);
+        d.bs_off_words = uint32_t(total);
+        total += round16w(N * bwords);
+        d.ba_off_words = uint32_t(total);
         total += round16w(N * bwords);
         d.bits = g.bits;
         d.len = g.max_len;
@@ -65,26 +71,33 @@ rmat_status build_image(rmat_table *t) {
         const PathTable &g = t->groups[gi];
         const GroupDesc &d = t->gdesc[gi];
         t->image[gi] = d.a_off_words;
-        t->image[kMaxGroups + gi] = d.b_off_words;
-        t->image[2 * kMaxGroups + gi] = uint32_t(g.bits);
+        t->image[kMaxGroups + gi] = d.bs_off_words;
+        t->image[2 * kMaxGroups + gi] = d.ba_off_words;
+        t->image[3 * kMaxGroups + gi] = uint32_t(g.bits);
         const size_t N = size_t(1) << g.bits;
+        const uint32_t C = uint32_t((uint64_t(1) << 32) >> g.bits);
         uint32_t *A = t->image.data() + d.a_off_words;
-        uint32_t *B = t->image.data() + d.b_off_words;
-        for (size_t j = 0; j < N; ++j) A[j] = (g.thr[j] << g.bits) | g.alias[j];
-        for (size_t i = 0; i < N; ++i) {
+        uint32_t *Bs = t->image.data() + d.bs_off_words;
+        uint32_t *Ba = t->image.data() + d.ba_off_words;
+        auto put_path = [&](uint32_t *B, size_t slot, size_t i) {
             const int L = g.len[i];
             uint32_t r, c;
             path_bits(g.sym[i], L, r, c);
             if (t->format == kCompact) {
                 const uint32_t r13 = L ? r << (13 - L) : 0u;
                 const uint32_t c13 = L ? c << (13 - L) : 0u;
-                B[i] = (r13 << 19) | (uint32_t(L) << 13) | c13;
+                B[slot] = (r13 << 19) | (uint32_t(L) << 13) | c13;
             } else {
-                B[4 * i + 0] = L ? r << (32 - L) : 0u;
-                B[4 * i + 1] = L ? c << (32 - L) : 0u;
-                B[4 * i + 2] = uint32_t(L);
-                B[4 * i + 3] = 0u;
+                B[4 * slot + 0] = L ? r << (32 - L) : 0u;
+                B[4 * slot + 1] = L ? c << (32 - L) : 0u;
+                B[4 * slot + 2] = uint32_t(L);
+                B[4 * slot + 3] = 0u;
             }
+        };
+        for (size_t j = 0; j < N; ++j) {
+            A[j] = uint32_t(j) * C + g.thr[j];  // thr < C, so no overflow
+            put_path(Bs, j, j);
+            put_path(Ba, j, g.alias[j]);
         }
     }
     return RMAT_OK;

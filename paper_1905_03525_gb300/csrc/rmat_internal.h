@@ -27,7 +27,7 @@ struct PathTable {
 };
 
 constexpr int kMaxGroups = 64;                 // level groups per table
-constexpr size_t kHeaderWords = 3 * kMaxGroups; // blob header: A offsets, B offsets, bits
+constexpr size_t kHeaderWords = 4 * kMaxGroups; // blob header: A, B-self, B-alias offsets, bits
 
 // Device table image formats (see rmat_image.cpp).
 enum ImageFormat : int {
@@ -36,8 +36,9 @@ enum ImageFormat : int {
 };
 
 struct GroupDesc {
-    uint32_t a_off_words;  // offset of A in the image, in u32 words
-    uint32_t b_off_words;  // offset of B in the image, in u32 words
+    uint32_t a_off_words;   // offset of A in the image, in u32 words
+    uint32_t bs_off_words;  // offset of B-self (path of column j)
+    uint32_t ba_off_words;  // offset of B-alias (path of alias[j])
     int bits;
     int len;               // levels of this group (per-level tables)
 };

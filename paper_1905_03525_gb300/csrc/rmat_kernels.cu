@@ -51,14 +51,30 @@ struct AccT<false> { using type = dev::Acc32; using word = uint32_t; };
 template <>
 struct AccT<true> { using type = dev::Acc64; using word = uint64_t; };
 
-// Where a warp keeps its tiles and queue, and which buffer is next.
+// Where a warp keeps its tiles and queue (shared address), and which buffer
+// is next.
 struct WarpState {
-    unsigned char *region;
+    uint32_t region;
     int tile;
     int buf;
     bool issued;  // a bulk store is (or may be) in flight
     int lane;
 };
+
+// Group 0 of the job's table from the job's own fields (kernel parameters:
+// uniform values, no shared-memory loads).
+template <bool SMEM>
+__device__ __forceinline__ dev::Group<SMEM> group0(const Job &J, uint32_t sblob) {
+    dev::Group<SMEM> G;
+    G.sA = sblob + 4u * J.a0;
+    G.sBs = sblob + 4u * J.bs0;
+    G.sBa = sblob + 4u * J.ba0;
+    G.gA = J.blob + J.a0;
+    G.gBs = J.blob + J.bs0;
+    G.gBa = J.blob + J.ba0;
+    G.mulb = 1u << J.bits0;
+    return G;
+}
 
 // Philox block q of edge e under the job's key.  KS: round keys read from the
 // job's precomputed schedule (kernel parameter), else derived in registers.
@@ -68,19 +84,24 @@ __device__ __forceinline__ uint4 edge_block(const Job &J, uint32_t q, uint64_t e
     else return dev::philox(q, 0u, uint32_t(e), uint32_t(e >> 32), J.key0, J.key1);
 }
 
+// Write edge `idx` of the tile at shared address `stage`.
+template <bool U64>
+__device__ __forceinline__ void put_pair(uint32_t stage, uint32_t idx, uint64_t r, uint64_t c) {
+    if constexpr (U64)
+        dev::sts128u64(stage + 16u * idx, r, c);
+    else
+        dev::sts64(stage + 8u * idx, uint32_t(r), uint32_t(c));
+}
+
 template <bool U64, bool UNDIR>
-__device__ __forceinline__ void put_final(unsigned char *stage, uint32_t idx, const typename AccT<U64>::type &acc,
-                                          int k) {
+__device__ __forceinline__ void put_final(uint32_t stage, uint32_t idx, const typename AccT<U64>::type &acc, int k) {
     uint64_t r = acc.out_row(k), c = acc.out_col(k);
     if (UNDIR && r > c) {
         const uint64_t t = r;
         r = c;
         c = t;
     }
-    if constexpr (U64)
-        reinterpret_cast<ulonglong2 *>(stage)[idx] = make_ulonglong2(r, c);
-    else
-        reinterpret_cast<uint2 *>(stage)[idx] = make_uint2(uint32_t(r), uint32_t(c));
+    put_pair<U64>(stage, idx, r, c);
 }
 
 // Phase 1 over a tile: one Philox block and up to `draws1` draws per edge,
@@ -91,7 +112,7 @@ __device__ __forceinline__ void put_final(unsigned char *stage, uint32_t idx, co
 // (bit i = edge i*32 + lane).
 template <int FMT, bool U64, bool SMEM, bool UNDIR, bool FULL, bool KS>
 __device__ __forceinline__ uint32_t phase1(const Job &J, const dev::Group<SMEM> &G0, uint64_t ebase, uint32_t n,
-                                           unsigned char *stage, uint8_t *p_fill, int lane) {
+                                           uint32_t stage, uint32_t p_fill, int lane) {
     using Acc = typename AccT<U64>::type;
     const uint32_t uk = uint32_t(J.k);
     uint32_t pm = 0;
@@ -112,11 +133,8 @@ __device__ __forceinline__ uint32_t phase1(const Job &J, const dev::Group<SMEM> 
             r = c;
             c = t;
         }
-        if constexpr (U64)
-            reinterpret_cast<ulonglong2 *>(stage)[idx] = make_ulonglong2(r, c);
-        else
-            reinterpret_cast<uint2 *>(stage)[idx] = make_uint2(uint32_t(r), uint32_t(c));
-        p_fill[idx] = uint8_t(acc.filled);
+        put_pair<U64>(stage, idx, r, c);
+        dev::sts8(p_fill + idx, acc.filled);
         pm |= uint32_t(!done) << it;
     };
     for (uint32_t it = 0; it < iters; it += 2) {
@@ -153,9 +171,9 @@ __device__ __forceinline__ void gen_tile(const Job &J, uint32_t sblob, const uin
     constexpr uint32_t EB = U64 ? 16 : 8;
     const int lane = W.lane;
     const uint32_t uk = uint32_t(J.k);
-    unsigned char *stage = W.region + W.buf * W.tile * EB;
-    uint8_t *p_fill = W.region + 2 * W.tile * EB;
-    uint16_t *p_q = reinterpret_cast<uint16_t *>(p_fill + W.tile);
+    const uint32_t stage = W.region + uint32_t(W.buf * W.tile) * EB;
+    const uint32_t p_fill = W.region + 2u * uint32_t(W.tile) * EB;   // 1 byte per edge
+    const uint32_t p_q = p_fill + uint32_t(W.tile);                  // 2 bytes per edge
     const uint64_t ebase = J.e0 + first;
 
     // The bulk store issued two tiles ago read this buffer; wait for it.
@@ -198,7 +216,7 @@ __device__ __forceinline__ void gen_tile(const Job &J, uint32_t sblob, const uin
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
         if (total) {
             uint32_t pos = incl - cnt;
-            for (uint32_t m = pm; m; m &= m - 1) p_q[pos++] = uint16_t((__ffs(m) - 1) * 32 + lane);
+            for (uint32_t m = pm; m; m &= m - 1) dev::sts16(p_q + 2u * pos++, (__ffs(m) - 1) * 32 + lane);
             __syncwarp();
             for (uint32_t pb = 0; pb < total; pb += 32) {
                 const bool has = pb + lane < total;
@@ -207,17 +225,17 @@ __device__ __forceinline__ void gen_tile(const Job &J, uint32_t sblob, const uin
                 acc.filled = uk;
                 uint32_t idx = 0;
                 if (has) {
-                    idx = p_q[pb + lane];
+                    idx = dev::lds16(p_q + 2u * (pb + lane));
                     if constexpr (U64) {
-                        const ulonglong2 v = reinterpret_cast<const ulonglong2 *>(stage)[idx];
+                        const ulonglong2 v = dev::lds128u64(stage + 16u * idx);
                         acc.row = v.x;
                         acc.col = v.y;
                     } else {
-                        const uint2 v = reinterpret_cast<const uint2 *>(stage)[idx];
+                        const uint2 v = dev::lds64(stage + 8u * idx);
                         acc.row = v.x;
                         acc.col = v.y;
                     }
-                    acc.filled = p_fill[idx];
+                    acc.filled = dev::lds8(p_fill + idx);
                 }
                 const uint64_t e = ebase + idx;
                 // every draw adds >= 1 level, so k <= 64 levels need <= 16 more
@@ -250,15 +268,14 @@ __device__ __forceinline__ void gen_tile(const Job &J, uint32_t sblob, const uin
         dev::fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) {
-            dev::bulk_s2g(gdst, stage, bytes);
+            dev::bulk_s2g_addr(gdst, stage, bytes);
             dev::bulk_commit();
         }
         W.issued = true;
     } else {
         __syncwarp();
-        const uint64_t *src = reinterpret_cast<const uint64_t *>(stage);
-        uint64_t *dst = reinterpret_cast<uint64_t *>(gdst);
-        for (uint32_t i = lane; i < bytes / 8; i += 32) dst[i] = src[i];
+        uint2 *dst = reinterpret_cast<uint2 *>(gdst);
+        for (uint32_t i = lane; i < bytes / 8; i += 32) dst[i] = dev::lds64(stage + 8u * i);
         __syncwarp();
     }
     W.buf ^= 1;
@@ -306,10 +323,10 @@ __global__ void __launch_bounds__(1024) k_alias(const __grid_constant__ Job J, i
         }
     }
     const uint32_t sblob = dev::smem_u32(s_blob);
-    const dev::Group<SMEM> G0 = dev::group<SMEM>(sblob, J.blob, 0);
+    const dev::Group<SMEM> G0 = group0<SMEM>(J, sblob);
 
     WarpState W;
-    W.region = s_blob + blob_bytes + size_t(warp) * warp_region_bytes(U64, LEVELS, tile);
+    W.region = dev::smem_u32(s_blob) + blob_bytes + uint32_t(warp) * warp_region_bytes(U64, LEVELS, tile);
     W.tile = tile;
     W.buf = 0;
     W.issued = false;
@@ -329,7 +346,7 @@ __global__ void __launch_bounds__(1024) k_alias(const __grid_constant__ Job J, i
 template <bool U64, int FMT, bool SMEM, bool LEVELS, bool UNDIR>
 __device__ __forceinline__ void batch_unit(const Job &J, uint32_t sblob, uint64_t local_unit, uint64_t unit_edges,
                                            int nwarps, int warp, WarpState &W) {
-    const dev::Group<SMEM> G0 = dev::group<SMEM>(sblob, J.blob, 0);
+    const dev::Group<SMEM> G0 = group0<SMEM>(J, sblob);
     const uint64_t f0 = local_unit * unit_edges;
     const uint64_t end = min(J.count, f0 + unit_edges);
     for (uint64_t first = f0 + uint64_t(warp) * W.tile; first < end; first += uint64_t(nwarps) * W.tile) {
@@ -355,7 +372,7 @@ __global__ void __launch_bounds__(1024) k_batch(BatchArgs B) {
         dev::fence_mbar_init();
     }
     WarpState W;
-    W.region = s_blob + B.max_blob_bytes + size_t(warp) * warp_region_bytes(U64, false, B.tile);
+    W.region = sblob + B.max_blob_bytes + uint32_t(warp) * warp_region_bytes(U64, false, B.tile);
     W.tile = B.tile;
     W.buf = 0;
     W.issued = false;
@@ -659,6 +676,10 @@ Job make_job(const rmat_table *t, const uint32_t *dblob, bool smem, uint64_t see
     J.out = out;
     J.fmt = uint32_t(t->format);
     J.smem = smem ? 1u : 0u;
+    J.a0 = t->gdesc[0].a_off_words;
+    J.bs0 = t->gdesc[0].bs_off_words;
+    J.ba0 = t->gdesc[0].ba_off_words;
+    J.bits0 = uint32_t(t->gdesc[0].bits);
     J.unit_begin = 0;
     return J;
 }

@@ -32,6 +32,8 @@ struct Job {
     uint32_t fmt;          // image format
     uint32_t smem;         // blob staged in shared memory
     uint32_t levels;       // draw g uses group g
+    uint32_t a0, bs0, ba0; // group 0: word offsets of A, Bs, Ba in the blob
+    uint32_t bits0;        // group 0: b
     uint64_t unit_begin;   // first work unit of this job (batches)
 };
 

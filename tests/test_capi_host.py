@@ -91,7 +91,7 @@ def test_table_info():
     info = rm.rmat_table_info(t)
     assert info["entries"] == 4093 and info["bits"] == 12 and info["index_bytes"] == 4
     assert info["max_len"] == 13 and info["groups"] == 1
-    assert info["device_image_bytes"] == 4096 * 8 + 3 * 64 * 4
+    assert info["device_image_bytes"] == 4096 * 12 + 4 * 64 * 4
     t64 = rm.rmat_build_table_levels(noisy_levels(34), 34, 6, rm.RMAT_UNDIRECTED)
     i64 = rm.rmat_table_info(t64)
     assert i64["index_bytes"] == 8 and i64["groups"] == 6 and i64["flags"] == 1

@@ -164,9 +164,13 @@ __device__ __forceinline__ uint32_t phase1(const Job &J, const dev::Group<SMEM> 
     return pm;
 }
 
+// sgroups: shared address of precomputed group descriptors (uint4 {A, Bs, Ba,
+// 2^b} per group) for per-level tables staged in shared memory, or 0 to read
+// them from the blob header at every draw.
 template <int FMT, bool U64, bool SMEM, bool LEVELS, bool UNDIR, bool KS>
 __device__ __forceinline__ void gen_tile(const Job &J, uint32_t sblob, const uint32_t *gblob,
-                                         const dev::Group<SMEM> &G0, uint64_t first, uint32_t n, WarpState &W) {
+                                         const dev::Group<SMEM> &G0, uint64_t first, uint32_t n, WarpState &W,
+                                         uint32_t sgroups = 0) {
     using Acc = typename AccT<U64>::type;
     constexpr uint32_t EB = U64 ? 16 : 8;
     const int lane = W.lane;
@@ -193,7 +197,16 @@ __device__ __forceinline__ void gen_tile(const Job &J, uint32_t sblob, const uin
                 for (int i = 0; i < 4; ++i) {
                     const int g = 4 * q + i;
                     if (g < J.ngroups) {
-                        const dev::Group<SMEM> Gg = dev::group<SMEM>(sblob, gblob, uint32_t(g));
+                        dev::Group<SMEM> Gg;
+                        if (SMEM && sgroups) {
+                            const uint4 gd = dev::lds128(sgroups + 16u * uint32_t(g));
+                            Gg.sA = gd.x;
+                            Gg.sBs = gd.y;
+                            Gg.sBa = gd.z;
+                            Gg.mulb = gd.w;
+                        } else {
+                            Gg = dev::group<SMEM>(sblob, gblob, uint32_t(g));
+                        }
                         dev::draw<FMT, SMEM>(Gg, ws[i], acc);
                     }
                 }
@@ -302,7 +315,9 @@ template <int FMT, bool U64, bool SMEM, bool LEVELS, bool UNDIR>
 __global__ void __launch_bounds__(1024) k_alias(const __grid_constant__ Job J, int tile, unsigned *err) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
-    unsigned char *s_blob = smem + 16;
+    // per-level tables in shared memory get 1 KB of precomputed group descriptors
+    constexpr uint32_t kGroupBytes = (LEVELS && SMEM) ? 16u * kMaxGroups : 0u;
+    unsigned char *s_blob = smem + 16 + kGroupBytes;
     const uint32_t blob_bytes = SMEM ? J.blob_bytes : 0;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -324,6 +339,16 @@ __global__ void __launch_bounds__(1024) k_alias(const __grid_constant__ Job J, i
     }
     const uint32_t sblob = dev::smem_u32(s_blob);
     const dev::Group<SMEM> G0 = group0<SMEM>(J, sblob);
+    uint32_t sgroups = 0;
+    if constexpr (LEVELS && SMEM) {
+        sgroups = dev::smem_u32(smem + 16);
+        for (int g = threadIdx.x; g < J.ngroups; g += blockDim.x) {
+            const dev::Group<true> Gg = dev::group<true>(sblob, J.blob, uint32_t(g));
+            uint4 *d = reinterpret_cast<uint4 *>(smem + 16) + g;
+            *d = make_uint4(Gg.sA, Gg.sBs, Gg.sBa, Gg.mulb);
+        }
+        __syncthreads();
+    }
 
     WarpState W;
     W.region = dev::smem_u32(s_blob) + blob_bytes + uint32_t(warp) * warp_region_bytes(U64, LEVELS, tile);
@@ -337,7 +362,7 @@ __global__ void __launch_bounds__(1024) k_alias(const __grid_constant__ Job J, i
         const uint64_t first = t * tile;
         const uint64_t left = J.count - first;
         const uint32_t n = left < uint64_t(tile) ? uint32_t(left) : uint32_t(tile);
-        gen_tile<FMT, U64, SMEM, LEVELS, UNDIR, true>(J, sblob, J.blob, G0, first, n, W);
+        gen_tile<FMT, U64, SMEM, LEVELS, UNDIR, true>(J, sblob, J.blob, G0, first, n, W, sgroups);
     }
     if (lane == 0 && W.issued) dev::bulk_wait_all();
 }
@@ -613,7 +638,8 @@ rmat_status plan_alias_launch(const rmat_table *t, const rmat_launch_config_t &w
     int tile = std::max(32, std::min(1024, want.tile_edges / 32 * 32));
     const int ctas = std::max(1, std::min(8, want.ctas_per_sm));
     auto need = [&](bool smem_table, int th, int tl) {
-        return size_t(16) + (smem_table ? img : 0) + size_t(th / 32) * warp_region_bytes(u64, levels, tl);
+        return size_t(16) + (smem_table ? img + (levels ? 16 * kMaxGroups : 0) : 0) +
+               size_t(th / 32) * warp_region_bytes(u64, levels, tl);
     };
     bool smem_table = true;
     // shrink the tile, then the CTA, until the table fits beside the warp tiles

@@ -249,7 +249,8 @@ typedef struct {
     int k;
     uint64_t m;           /* edges 0..m-1 of the graph, m >= 1 */
     uint64_t seed;
-    uint64_t table_bound; /* variable-length table bound; 0 = 4096 */
+    uint64_t table_bound; /* variable-length table bound; 0 = the largest power of two <= 4096
+                             whose table the batched kernel can keep in shared memory */
     unsigned flags;       /* RMAT_UNDIRECTED or 0 */
 } rmat_request_t;
 
@@ -266,6 +267,7 @@ typedef struct {
     uint64_t checksum;
     double submit_s, admit_s, done_s;
     rmat_status error;    /* why the request failed, if it did */
+    uint64_t table_bound; /* the bound the request's table was built with */
 } rmat_request_status_t;
 
 typedef struct {

@@ -50,7 +50,7 @@ class Request(ctypes.Structure):
 class RequestStatus(ctypes.Structure):
     _fields_ = [("id", ctypes.c_uint64), ("state", ctypes.c_int), ("edges_done", ctypes.c_uint64),
                 ("checksum", ctypes.c_uint64), ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
-                ("done_s", ctypes.c_double), ("error", ctypes.c_int)]
+                ("done_s", ctypes.c_double), ("error", ctypes.c_int), ("table_bound", ctypes.c_uint64)]
 
 
 class ServerStats(ctypes.Structure):

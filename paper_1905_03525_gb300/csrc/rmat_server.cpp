@@ -360,6 +360,7 @@ void fill_status(const Request *r, rmat_request_status_t *st) {
     st->admit_s = r->t_admit;
     st->done_s = r->t_done;
     st->error = r->err;
+    st->table_bound = r->desc.table_bound;
 }
 
 }  // namespace
@@ -420,9 +421,21 @@ rmat_status rmat_server_submit(rmat_server *s, const rmat_request_t *req, uint64
     clear_error();
     if (!s || !req) return fail(RMAT_ERR_INVALID_ARGUMENT, "NULL argument");
     if (req->m == 0) return fail(RMAT_ERR_INVALID_ARGUMENT, "a request needs m >= 1 edges");
-    const uint64_t bound = req->table_bound ? req->table_bound : 4096;
+    // table_bound 0: the largest power-of-two bound <= 4096 whose blob the
+    // batched kernel can stage in shared memory (deep paths of skewed
+    // parameters make wide, 36-byte columns); otherwise exactly the bound asked.
+    const bool u64 = req->k > 32;
+    const size_t smem_budget = size_t(s->props.max_smem) - 16 -
+                               size_t(kThreads / 32) * warp_bytes(u64, false, tile_for(u64));
+    uint64_t bound = req->table_bound ? req->table_bound : 4096;
     rmat_table *t = nullptr;
-    if (rmat_status st = rmat_build_table(req->a, req->b, req->c, req->d, req->k, bound, &t)) return st;
+    for (;;) {
+        if (rmat_status st = rmat_build_table(req->a, req->b, req->c, req->d, req->k, bound, &t)) return st;
+        if (req->table_bound || t->image.size() * 4 <= smem_budget || bound <= 64) break;
+        rmat_free_table(t);
+        t = nullptr;
+        bound /= 2;
+    }
     if (rmat_status st = rmat_table_set_flags(t, req->flags)) {
         rmat_free_table(t);
         return st;
@@ -440,6 +453,7 @@ rmat_status rmat_server_submit(rmat_server *s, const rmat_request_t *req, uint64
         return fail(RMAT_ERR_OUT_OF_MEMORY, "host allocation failed");
     }
     r->desc = *req;
+    r->desc.table_bound = bound;
     r->table = t;
     {
         std::lock_guard<std::mutex> lk(s->mu);

@@ -80,7 +80,7 @@ class Server:
             pass
 
 
-def run_trace(server: Server, trace, submitters: int = 8, table_bound: int = 4096):
+def run_trace(server: Server, trace, submitters: int = 8, table_bound: int = 0):
     """Submit every request of `trace` at its arrival time (seconds after the
     start), wait for all, and return per-request records."""
     ids = [None] * len(trace)
@@ -111,7 +111,7 @@ def run_trace(server: Server, trace, submitters: int = 8, table_bound: int = 409
     out = []
     for r, rid in zip(trace, ids):
         st = server.status(rid)
-        out.append({**r, "id": rid, "state": st["state"], "checksum": st["checksum"],
+        out.append({**r, "id": rid, "state": st["state"], "checksum": st["checksum"], "table_bound": st["table_bound"],
                     "latency_s": st["done_s"] - st["submit_s"], "queue_s": st["admit_s"] - st["submit_s"],
                     "submit_s": st["submit_s"] - clock0, "done_s": st["done_s"] - clock0})
     return out

@@ -66,8 +66,10 @@ def test_results_same_alone_and_in_the_mix():
     assert all(x["state"] == DONE and x["edges_done"] == m for x, (_, _, m, _) in zip(mixed, REQS))
     assert st["steps"] > len(REQS)  # multi-chunk requests really were split
     for x, (p, k, m, s) in zip(mixed, REQS):
-        r, c = alone(p, k, m, s)
+        r, c = alone(p, k, m, s, x["table_bound"])
         assert x["checksum"] == host_checksum(r, c, 0), (k, m)
+    # auto bounds: deep (wide-entry) tables were shrunk to fit shared memory
+    assert mixed[1]["table_bound"] < 4096 and mixed[0]["table_bound"] == 4096
     # one request alone on its own server gives the same checksum
     with Server(64 << 20, chunk_edges=1 << 20, step_edges=1 << 20, max_active=1) as srv:
         p, k, m, s = REQS[1]
@@ -97,20 +99,22 @@ def test_chunk_callback_sees_every_edge():
         assert rt.cudaMemcpy(buf.ctypes.data, ptr, cnt * eb, 2) == 0
         got[rid]["parts"].append((off, buf))
 
-    reqs = [(G500, 26, 50_001, 11), (SKEWED, 40, 33_000, 12), (G500, 12, 777, 13)]
+    reqs = [(G500, 26, 50_001, 11, 0), (SKEWED, 40, 33_000, 12, 4096), (G500, 12, 777, 13, 0)]
     with Server(128 << 20, chunk_edges=8192, step_edges=1 << 15, max_active=3) as srv:
         srv.set_chunk_callback(on_chunk)
-        for p, k, m, s in reqs:
-            rid = srv.submit(*p, k, m, s)
+        for p, k, m, s, bound in reqs:
+            rid = srv.submit(*p, k, m, s, bound)
             got[rid] = {"eb": 8 if k <= 32 else 16, "parts": [], "req": (p, k, m, s)}
         srv.drain(600)
+        bounds = {rid: srv.status(rid)["table_bound"] for rid in got}
+    assert sorted(bounds.values()) == [4096, 4096, 4096]   # explicit bound kept; G500 fits
     for rid, g in got.items():
         p, k, m, s = g["req"]
         parts = sorted(g["parts"], key=lambda x: x[0])
         assert [o for o, _ in parts] == list(range(0, m, 8192))
         data = np.concatenate([b for _, b in parts])
         data = data.view(np.uint32 if k <= 32 else np.uint64).reshape(-1, 2)
-        r, c = alone(p, k, m, s)
+        r, c = alone(p, k, m, s, bounds[rid])
         assert np.array_equal(data[:, 0].astype(np.uint64), r) and np.array_equal(data[:, 1].astype(np.uint64), c)
 
 

@@ -25,7 +25,7 @@ from . import (rmat_batch_add, rmat_batch_create, rmat_batch_launch, rmat_batch_
                rmat_build_table_fixed, rmat_build_table_levels, rmat_generate, rmat_set_launch_config,
                rmat_table_info, empty_edges)
 
-LAUNCH_SHAPES = [(1024, 1, 256), (1024, 1, 512), (768, 1, 256), (512, 2, 256), (512, 1, 512), (256, 4, 256)]
+LAUNCH_SHAPES = [(1024, 1, 512), (1024, 1, 256), (768, 1, 512), (512, 2, 512), (512, 1, 1024), (256, 4, 512)]
 BOUNDS = [1 << b for b in range(8, 15)]
 ELLS = [4, 5, 6, 7, 8]
 _lock = threading.Lock()
@@ -172,7 +172,7 @@ def batch_blob_budget(threads: int = 1024, tile: int = 256, u64: bool = False) -
     """Shared memory the batched kernel has left for a staged table blob."""
     import torch
     smem = torch.cuda.get_device_properties(torch.cuda.current_device()).shared_memory_per_block_optin
-    per_warp = 2 * tile * (16 if u64 else 8) + 3 * tile
+    per_warp = tile * (16 if u64 else 8) + 3 * tile
     return smem - 16 - (threads // 32) * per_warp
 
 

@@ -276,9 +276,9 @@ __device__ __forceinline__ void bulk_commit() {
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 
-// Wait until at most one committed group is still reading shared memory.
-__device__ __forceinline__ void bulk_wait_read_1() {
-    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+// Wait until every committed group has finished reading shared memory.
+__device__ __forceinline__ void bulk_wait_read_0() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
 __device__ __forceinline__ void bulk_wait_all() {

@@ -10,8 +10,7 @@
 //            32 at a time with further Philox blocks, so that the rare long
 //            edges do not make every lane of a warp pay for a second block.
 //   Edges are written into a per-warp shared tile that leaves with one TMA
-//   bulk store (double-buffered: the store of one tile overlaps the sampling
-//   of the next).
+//   bulk store (asynchronous: it overlaps the sampling of the next tile).
 // Per-level tables (Sec. 3, one table per level group) take exactly one draw
 // per group, with no phase 2.
 //
@@ -37,11 +36,14 @@ namespace {
 
 constexpr uint32_t kWaitLimit = 1u << 22;
 
-// Bytes of one warp's shared region: two output tiles, the level count of
+// Bytes of one warp's shared region: the output tile, the level count of
 // every unfinished edge (1 byte per edge) and the queue of unfinished edges
-// (2 bytes per edge).
+// (2 bytes per edge).  One tile buffer is enough: the bulk store of a tile
+// has read its few KB out of shared memory long before the warp has sampled
+// the next tile, and the memory saved buys larger tiles (fuller phase-2
+// batches).
 __host__ __device__ constexpr uint32_t warp_region_bytes(bool u64, bool levels, int tile) {
-    return 2u * uint32_t(tile) * (u64 ? 16u : 8u) + (levels ? 0u : 3u * uint32_t(tile));
+    return uint32_t(tile) * (u64 ? 16u : 8u) + (levels ? 0u : 3u * uint32_t(tile));
 }
 
 template <bool U64>
@@ -51,12 +53,10 @@ struct AccT<false> { using type = dev::Acc32; using word = uint32_t; };
 template <>
 struct AccT<true> { using type = dev::Acc64; using word = uint64_t; };
 
-// Where a warp keeps its tiles and queue (shared address), and which buffer
-// is next.
+// Where a warp keeps its tile and queue (shared address).
 struct WarpState {
     uint32_t region;
     int tile;
-    int buf;
     bool issued;  // a bulk store is (or may be) in flight
     int lane;
 };
@@ -175,13 +175,13 @@ __device__ __forceinline__ void gen_tile(const Job &J, uint32_t sblob, const uin
     constexpr uint32_t EB = U64 ? 16 : 8;
     const int lane = W.lane;
     const uint32_t uk = uint32_t(J.k);
-    const uint32_t stage = W.region + uint32_t(W.buf * W.tile) * EB;
-    const uint32_t p_fill = W.region + 2u * uint32_t(W.tile) * EB;   // 1 byte per edge
+    const uint32_t stage = W.region;
+    const uint32_t p_fill = W.region + uint32_t(W.tile) * EB;        // 1 byte per edge
     const uint32_t p_q = p_fill + uint32_t(W.tile);                  // 2 bytes per edge
     const uint64_t ebase = J.e0 + first;
 
-    // The bulk store issued two tiles ago read this buffer; wait for it.
-    if (lane == 0 && W.issued) dev::bulk_wait_read_1();
+    // The bulk store of the previous tile must have read the buffer.
+    if (lane == 0 && W.issued) dev::bulk_wait_read_0();
     __syncwarp();
 
     if constexpr (LEVELS) {
@@ -291,7 +291,6 @@ __device__ __forceinline__ void gen_tile(const Job &J, uint32_t sblob, const uin
         for (uint32_t i = lane; i < bytes / 8; i += 32) dst[i] = dev::lds64(stage + 8u * i);
         __syncwarp();
     }
-    W.buf ^= 1;
 }
 
 // Stage a blob into shared memory with one bulk copy (chunks of 32 KB) on
@@ -353,7 +352,6 @@ __global__ void __launch_bounds__(1024) k_alias(const __grid_constant__ Job J, i
     WarpState W;
     W.region = dev::smem_u32(s_blob) + blob_bytes + uint32_t(warp) * warp_region_bytes(U64, LEVELS, tile);
     W.tile = tile;
-    W.buf = 0;
     W.issued = false;
     W.lane = lane;
     const uint64_t ntiles = (J.count + tile - 1) / tile;
@@ -399,7 +397,6 @@ __global__ void __launch_bounds__(1024) k_batch(BatchArgs B) {
     WarpState W;
     W.region = sblob + B.max_blob_bytes + uint32_t(warp) * warp_region_bytes(U64, false, B.tile);
     W.tile = B.tile;
-    W.buf = 0;
     W.issued = false;
     W.lane = lane;
 
@@ -621,7 +618,7 @@ rmat_launch_config_t default_launch_config(const rmat_table *t) {
     rmat_launch_config_t c;
     c.threads = 1024;
     c.ctas_per_sm = 1;
-    c.tile_edges = t->k > 32 ? 128 : 256;
+    c.tile_edges = t->k > 32 ? 256 : 512;
     return c;
 }
 

@@ -711,10 +711,15 @@ rmat_status launch_alias(const rmat_table *t, const uint32_t *dblob, const Alias
                          uint64_t e0, uint64_t count, void *out, cudaStream_t stream) {
     if (count == 0) return RMAT_OK;
     Job J = make_job(t, dblob, plan.smem_table, seed, e0, count, out);
-    int tile = plan.tile;
     unsigned *err = plan.err;
     const int warps = plan.threads / 32;
-    const uint64_t ntiles = (count + plan.tile - 1) / plan.tile;
+    // Small launches: smaller tiles (down to 64 edges) until every warp of a
+    // full grid has a tile.  A smaller tile fits in the planned shared memory,
+    // and the bytes written never depend on the tile size.
+    int tile = plan.tile;
+    const uint64_t grid_warps = uint64_t(plan.sms) * plan.ctas_per_sm * warps;
+    while (tile > 64 && tile % 64 == 0 && (count + tile - 1) / tile < grid_warps) tile /= 2;
+    const uint64_t ntiles = (count + tile - 1) / tile;
     const uint64_t want_ctas = (ntiles + warps - 1) / warps;
     const uint64_t max_ctas = uint64_t(plan.sms) * plan.ctas_per_sm;
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want_ctas, max_ctas)));

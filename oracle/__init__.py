@@ -44,36 +44,45 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def load(path: str):
+    """Load an oracle shared library and declare its functions."""
+    L = ctypes.CDLL(path)
+    _declare(L)
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = build()
-            L = ctypes.CDLL(path)
-            u32, u64, i32, dbl = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_double
-            vp = ctypes.c_void_p
-            L.orc_philox4x32_10.argtypes = [vp, vp, vp]
-            L.orc_word.argtypes = [u64, u64, u64]
-            L.orc_word.restype = u32
-            L.orc_table_variable.argtypes = [dbl, dbl, dbl, dbl, i32, u64]
-            L.orc_table_variable.restype = vp
-            L.orc_table_fixed.argtypes = [vp, i32]
-            L.orc_table_fixed.restype = vp
-            L.orc_table_free.argtypes = [vp]
-            for name in ("orc_table_entries", "orc_table_bits", "orc_table_max_len"):
-                getattr(L, name).argtypes = [vp]
-                getattr(L, name).restype = i32
-            L.orc_table_get.argtypes = [vp] * 7
-            L.orc_draw.argtypes = [vp, u32]
-            L.orc_draw.restype = u32
-            L.orc_generate.argtypes = [vp, i32, i32, i32, u64, u64, u64, vp, vp]
-            L.orc_generate.restype = i32
-            L.orc_generate_naive.argtypes = [vp, i32, i32, u64, u64, u64, vp, vp]
-            L.orc_generate_naive.restype = i32
-            L.orc_edge_distribution.argtypes = [vp, i32, i32, i32, vp]
-            L.orc_edge_distribution.restype = i32
-            _lib = L
+            _lib = load(build())
     return _lib
+
+
+def _declare(L):
+    """Argument and result types of the oracle's C functions."""
+    u32, u64, i32, dbl = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_double
+    vp = ctypes.c_void_p
+    L.orc_philox4x32_10.argtypes = [vp, vp, vp]
+    L.orc_word.argtypes = [u64, u64, u64]
+    L.orc_word.restype = u32
+    L.orc_table_variable.argtypes = [dbl, dbl, dbl, dbl, i32, u64]
+    L.orc_table_variable.restype = vp
+    L.orc_table_fixed.argtypes = [vp, i32]
+    L.orc_table_fixed.restype = vp
+    L.orc_table_free.argtypes = [vp]
+    for name in ("orc_table_entries", "orc_table_bits", "orc_table_max_len"):
+        getattr(L, name).argtypes = [vp]
+        getattr(L, name).restype = i32
+    L.orc_table_get.argtypes = [vp] * 7
+    L.orc_draw.argtypes = [vp, u32]
+    L.orc_draw.restype = u32
+    L.orc_generate.argtypes = [vp, i32, i32, i32, u64, u64, u64, vp, vp]
+    L.orc_generate.restype = i32
+    L.orc_generate_naive.argtypes = [vp, i32, i32, u64, u64, u64, vp, vp]
+    L.orc_generate_naive.restype = i32
+    L.orc_edge_distribution.argtypes = [vp, i32, i32, i32, vp]
+    L.orc_edge_distribution.restype = i32
 
 
 def _ptr(a: np.ndarray):

@@ -1,0 +1,71 @@
+"""The oracle's pins catch plausible slips.  Each case copies the oracle's C
+source, plants one mistake (a dropped term, a swapped operand, an off-by-one),
+compiles it on the CPU and runs pins from test_oracle_pins.py against it; at
+least one must fail.  Nothing here touches a GPU."""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "rmat_oracle.c")
+
+MUTATIONS = [
+    ("b and c swapped in the expansion", "child.p = e.p * P[s];",
+     "child.p = e.p * P[s == 1 ? 2 : (s == 2 ? 1 : s)];",
+     [lambda: pins.test_exact_distribution_equals_kronecker(*list(pins._distribution_cases())[5])]),
+    ("row and column bits swapped", "                r = (r << 1) | (uint64_t)(s >> 1);\n                c = (c << 1) | (uint64_t)(s & 1);\n            }\n            filled += take;",
+     "                r = (r << 1) | (uint64_t)(s & 1);\n                c = (c << 1) | (uint64_t)(s >> 1);\n            }\n            filled += take;",
+     [lambda: pins.test_per_level_quadrant_frequencies("alias_variable")]),
+    ("stop rule off by one", "heap.n + ndone + 3 < bound", "heap.n + ndone + 3 <= bound",
+     [lambda: pins.test_table_sizes_fig1("variable", 12, 4093)]),
+    ("Philox multiplier typo", "#define PHILOX_M0 0xD2511F53u", "#define PHILOX_M0 0xD2511F35u",
+     [pins.test_philox_matches_independent_engine]),
+    ("Philox output words rotated", "return out[n % 4];", "return out[(n + 1) % 4];",
+     [pins.test_philox_matches_independent_engine]),
+    ("Vose drops a term", "rest[l] -= C - rest[s];", "rest[l] -= C;",
+     [lambda: pins.test_weights_and_alias_roundtrip(lambda: oracle.Table.fixed([pins.ASYM], 4))]),
+    ("remainder to the smallest fractions", "if (a->frac != b->frac) return (a->frac < b->frac) - (a->frac > b->frac);",
+     "if (a->frac != b->frac) return (a->frac > b->frac) - (a->frac < b->frac);",
+     [lambda: pins.test_weights_and_alias_roundtrip(lambda: oracle.Table.variable(*pins.G500, 26, 4096))]),
+    ("draw keeps the column on equality", "return r < t->thr[j] ? j : t->alias[j];", "return r <= t->thr[j] ? j : t->alias[j];",
+     [pins.test_draw_keeps_column_with_probability_thr_over_C_exactly]),
+    ("naive sampler uses a+c for the second threshold", "T[3 * lvl + 1] = naive_threshold(P[0] + P[1]);",
+     "T[3 * lvl + 1] = naive_threshold(P[0] + P[2]);",
+     [lambda: pins.test_per_level_quadrant_frequencies("naive")]),
+    ("undirected keeps the larger index first", "if (undirected && r > c) { uint64_t tmp = r; r = c; c = tmp; }\n        row[i] = r;\n        col[i] = c;\n    }\n    return 0;\n}\n\n/* Threshold",
+     "if (undirected && r < c) { uint64_t tmp = r; r = c; c = tmp; }\n        row[i] = r;\n        col[i] = c;\n    }\n    return 0;\n}\n\n/* Threshold",
+     [pins.test_undirected_mirrors_lower_triangle]),
+]
+
+
+def _build_mutant(tmp_path, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, old
+    path = tmp_path / "mutant.c"
+    path.write_text(src.replace(old, new))
+    hdr = os.path.join(os.path.dirname(SRC), "rmat_oracle.h")
+    (tmp_path / "rmat_oracle.h").write_text(open(hdr).read())
+    so = tmp_path / "mutant.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", str(so), str(path), "-lm"],
+                   check=True)
+    return oracle.load(str(so))
+
+
+@pytest.mark.parametrize("name,old,new,checks", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(tmp_path, name, old, new, checks):
+    mutant = _build_mutant(tmp_path, old, new)
+    saved = oracle._lib
+    oracle._lib = mutant
+    try:
+        caught = False
+        for check in checks:
+            try:
+                check()
+            except (AssertionError, ValueError):
+                caught = True
+        assert caught, f"no pin caught: {name}"
+    finally:
+        oracle._lib = saved

@@ -397,3 +397,21 @@ def test_invalid_arguments_rejected():
         oracle.Table.variable(-0.1, 0.5, 0.5, 0.1, 10, 4096)
     with pytest.raises(ValueError):
         oracle.Table.fixed([G500], 13)
+
+
+def test_draw_keeps_column_with_probability_thr_over_C_exactly():
+    """Walker's alias method: a draw landing in column j keeps j for exactly
+    thr[j] of the C residuals and yields alias[j] for the others.  With a
+    4^12-entry table C = 256, so every residual of a column can be tried; with
+    the exact weight reconstruction above this pins P(entry) = w / 2^32."""
+    t = oracle.Table.fixed([ASYM], 12)
+    b = t.bits
+    C = 1 << (32 - b)
+    for j in list(range(0, 1 << b, 262139))[:64]:
+        sel = [t.draw((j << (32 - b)) | r) for r in range(C)]
+        keep = sum(1 for s in sel if s == j)
+        if int(t.alias[j]) == j:
+            assert keep == C
+        else:
+            assert keep == int(t.thr[j])
+            assert all(s == t.alias[j] for s in sel[int(t.thr[j]):])

@@ -259,6 +259,11 @@ def run_ours(args):
 
     # comparator: the naive per-bit kernel (k quadrant draws per edge) on the same workload
     naive_s = _events_time(lambda: rm.rmat_generate_naive(G500, K, 0, SEED, e0, m, out, stream), stream, 2)
+    # the same launch with scrambled vertex IDs (the relabelling fused into the store)
+    scr_table = rm.rmat_build_table(*G500, K, BOUND)
+    rm.rmat_table_set_scramble(scr_table, True, SEED)
+    rm.rmat_generate(scr_table, SEED, e0, m, out, stream)
+    scr_s = _events_time(lambda: rm.rmat_generate(scr_table, SEED, e0, m, out, stream), stream, 3)
     # restore this step's output of the alias kernel
     rm.rmat_generate(table, SEED, e0, m, out, stream)
     stream.synchronize()
@@ -307,7 +312,10 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": 8 * m, "avg_launch_ms": avg_launch_s * 1e3},
         "cpu_baseline": cb,
         "comparators": {"naive_per_bit_gpu": {"value": world * m / naive_s, "unit": "edges/s",
-                                              "note": "k Philox words and quadrant draws per edge, same GPU"}},
+                                              "note": "k Philox words and quadrant draws per edge, same GPU"},
+                        "scrambled_ids": {"value": world * m / scr_s, "unit": "edges/s",
+                                          "overhead_ns_per_edge": (scr_s - avg_launch_s) / m * 1e9,
+                                          "note": "same launch with rmat_table_set_scramble on"}},
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": {"sm_mhz": cs["sm_mhz"], "sm_max_mhz": cs["sm_max_mhz"], "reasons": cs["reasons"]},

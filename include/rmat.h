@@ -104,6 +104,18 @@ rmat_status rmat_build_table_levels(const double *abcd, int k, int ell, unsigned
 /* Set or clear flags (RMAT_UNDIRECTED) on an existing table. */
 rmat_status rmat_table_set_flags(rmat_table *t, unsigned flags);
 
+/*
+ * rmat_table_set_scramble -- relabel vertex IDs by a seeded bijection pi of
+ * [0, 2^k) (Sec. 3: scrambling is a constant-time post-processing that hides
+ * the graph's structure, as Graph 500 does).  Each edge (r, c) becomes
+ * (pi(r), pi(c)), before undirected mirroring.  pi: three rounds of
+ *   x ^= x >> ceil(k/2);  x = (x * m_i + a_i) mod 2^k      (m_i odd),
+ * each round a bijection; m_0, a_0, m_1, a_1, m_2, a_2 are the first six
+ * outputs of SplitMix64 seeded with scramble_seed, reduced mod 2^k (the m_i
+ * with their low bit set).  enable = 0 turns it off.
+ */
+rmat_status rmat_table_set_scramble(rmat_table *t, int enable, uint64_t scramble_seed);
+
 typedef struct {
     int k;              /* levels */
     int groups;         /* 1, or the number of level groups */
@@ -252,6 +264,8 @@ typedef struct {
     uint64_t table_bound; /* variable-length table bound; 0 = the largest power of two <= 4096
                              whose table the batched kernel can keep in shared memory */
     unsigned flags;       /* RMAT_UNDIRECTED or 0 */
+    int scramble;         /* nonzero: relabel vertices as rmat_table_set_scramble(t, 1, scramble_seed) */
+    uint64_t scramble_seed;
 } rmat_request_t;
 
 enum { RMAT_REQ_QUEUED = 0, RMAT_REQ_RUNNING = 1, RMAT_REQ_DONE = 2, RMAT_REQ_FAILED = 3 };

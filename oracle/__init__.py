@@ -83,6 +83,11 @@ def _declare(L):
     L.orc_generate_naive.restype = i32
     L.orc_edge_distribution.argtypes = [vp, i32, i32, i32, vp]
     L.orc_edge_distribution.restype = i32
+    L.orc_scramble_constants.argtypes = [u64, i32, vp]
+    L.orc_scramble.argtypes = [u64, i32, vp]
+    L.orc_scramble.restype = u64
+    L.orc_generate_scrambled.argtypes = [vp, i32, i32, i32, vp, u64, u64, u64, vp, vp]
+    L.orc_generate_scrambled.restype = i32
 
 
 def _ptr(a: np.ndarray):
@@ -159,6 +164,30 @@ def generate(tables, k, seed, e0, count, undirected=False):
     col = np.zeros(count, np.uint64)
     h = _handles(tables)
     rc = lib().orc_generate(h, len(tables), k, int(undirected), seed, e0, count, _ptr(row), _ptr(col))
+    if rc != 0:
+        raise ValueError("oracle rejected the generate arguments")
+    return row, col
+
+
+def scramble_constants(scramble_seed: int, k: int) -> np.ndarray:
+    out = np.zeros(6, np.uint64)
+    lib().orc_scramble_constants(scramble_seed, k, _ptr(out))
+    return out
+
+
+def scramble(x: int, k: int, consts) -> int:
+    c = np.ascontiguousarray(consts, dtype=np.uint64)
+    return int(lib().orc_scramble(x, k, _ptr(c)))
+
+
+def generate_scrambled(tables, k, scramble_seed, seed, e0, count, undirected=False):
+    """orc_generate followed by the vertex relabelling of scramble_seed."""
+    tables = list(tables)
+    consts = scramble_constants(scramble_seed, k)
+    row = np.zeros(count, np.uint64)
+    col = np.zeros(count, np.uint64)
+    rc = lib().orc_generate_scrambled(_handles(tables), len(tables), k, int(undirected), _ptr(consts), seed, e0,
+                                      count, _ptr(row), _ptr(col))
     if rc != 0:
         raise ValueError("oracle rejected the generate arguments")
     return row, col

@@ -367,8 +367,38 @@ uint32_t orc_draw(const orc_table *t, uint32_t u)
 /* ------------------------------------------------------------------ */
 /* Sampling loop (Sec. 2 sampling-loop fragment, with reading R8)      */
 /* ------------------------------------------------------------------ */
-int orc_generate(const orc_table *const *tables, int ngroups, int k, int undirected,
-                 uint64_t seed, uint64_t e0, uint64_t count, uint64_t *row, uint64_t *col)
+static uint64_t splitmix64_next(uint64_t *state)
+{
+    uint64_t z = (*state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+void orc_scramble_constants(uint64_t scramble_seed, int k, uint64_t out[6])
+{
+    uint64_t mask = k >= 64 ? ~0ull : ((1ull << k) - 1);
+    uint64_t st = scramble_seed;
+    for (int i = 0; i < 3; ++i) {
+        out[2 * i] = (splitmix64_next(&st) | 1ull) & mask;
+        out[2 * i + 1] = splitmix64_next(&st) & mask;
+    }
+}
+
+uint64_t orc_scramble(uint64_t x, int k, const uint64_t c[6])
+{
+    uint64_t mask = k >= 64 ? ~0ull : ((1ull << k) - 1);
+    int h = (k + 1) / 2;
+    for (int i = 0; i < 3; ++i) {
+        x ^= x >> h;
+        x = (x * c[2 * i] + c[2 * i + 1]) & mask;
+    }
+    return x;
+}
+
+int orc_generate_scrambled(const orc_table *const *tables, int ngroups, int k, int undirected,
+                           const uint64_t *consts, uint64_t seed, uint64_t e0, uint64_t count,
+                           uint64_t *row, uint64_t *col)
 {
     if (ngroups < 1 || k < 1 || k > 64) return -1;
     if (ngroups > 1) {
@@ -395,11 +425,21 @@ int orc_generate(const orc_table *const *tables, int ngroups, int k, int undirec
             }
             filled += take;
         }
+        if (consts) {
+            r = orc_scramble(r, k, consts);
+            c = orc_scramble(c, k, consts);
+        }
         if (undirected && r > c) { uint64_t tmp = r; r = c; c = tmp; }
         row[i] = r;
         col[i] = c;
     }
     return 0;
+}
+
+int orc_generate(const orc_table *const *tables, int ngroups, int k, int undirected,
+                 uint64_t seed, uint64_t e0, uint64_t count, uint64_t *row, uint64_t *col)
+{
+    return orc_generate_scrambled(tables, ngroups, k, undirected, NULL, seed, e0, count, row, col);
 }
 
 /* Threshold round(x 2^32), saturated to 2^32 - 1. */

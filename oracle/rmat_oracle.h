@@ -72,6 +72,21 @@ uint32_t orc_draw(const orc_table *t, uint32_t u);
 int orc_generate(const orc_table *const *tables, int ngroups, int k, int undirected,
                  uint64_t seed, uint64_t e0, uint64_t count, uint64_t *row, uint64_t *col);
 
+/* Scrambling (Sec. 3: Graph 500 hides the structure by relabelling vertex IDs;
+ * a constant-time post-processing).  pi is a bijection of [0, 2^k): three
+ * rounds of x ^= x >> ceil(k/2); x = (x * m_i + a_i) mod 2^k, with odd m_i.
+ * The constants come from the scramble seed through SplitMix64 (Steele, Lea,
+ * Flood 2014): m_0, a_0, m_1, a_1, m_2, a_2 are its first six outputs, each
+ * reduced mod 2^k, the m_i with their low bit set. */
+void orc_scramble_constants(uint64_t scramble_seed, int k, uint64_t out[6]);
+uint64_t orc_scramble(uint64_t x, int k, const uint64_t consts[6]);
+
+/* orc_generate with optional scrambling (consts != NULL): both endpoints are
+ * relabelled by pi before undirected mirroring. */
+int orc_generate_scrambled(const orc_table *const *tables, int ngroups, int k, int undirected,
+                           const uint64_t *consts, uint64_t seed, uint64_t e0, uint64_t count,
+                           uint64_t *row, uint64_t *col);
+
 /* Naive per-bit R-MAT (Sec. 1): level t draws one quadrant from word t with
  * thresholds round(a 2^32), round((a+b) 2^32), round((a+b+c) 2^32) of the
  * level's normalised parameters P[4t..4t+3]. */

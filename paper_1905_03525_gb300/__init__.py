@@ -16,7 +16,7 @@ from ._capi import (RMAT_UNDIRECTED, LaunchConfig, RmatError, TableInfo, check, 
 
 __all__ = [
     "RMAT_UNDIRECTED", "RmatError", "Table", "rmat_build_table", "rmat_build_table_fixed",
-    "rmat_build_table_levels", "rmat_table_set_flags", "rmat_table_info", "rmat_table_group_info",
+    "rmat_build_table_levels", "rmat_table_set_flags", "rmat_table_set_scramble", "rmat_table_info", "rmat_table_group_info",
     "rmat_table_export", "rmat_table_upload", "rmat_free_table", "rmat_generate", "rmat_generate_host",
     "rmat_generate_naive", "rmat_set_launch_config", "rmat_get_launch_config",
     "rmat_check_device_errors", "rmat_version", "edge_bytes", "empty_edges", "Batch", "rmat_batch_create",
@@ -101,6 +101,11 @@ def rmat_build_table_levels(abcd, k, ell, flags=0) -> Table:
 
 def rmat_table_set_flags(t: Table, flags: int) -> None:
     check(lib().rmat_table_set_flags(t.handle, flags))
+
+
+def rmat_table_set_scramble(t: Table, enable: bool, scramble_seed: int = 0) -> None:
+    """Relabel vertex IDs by the seeded bijection of include/rmat.h (Sec. 3 scrambling)."""
+    check(lib().rmat_table_set_scramble(t.handle, int(bool(enable)), scramble_seed))
 
 
 def rmat_table_info(t: Table) -> dict:

@@ -44,7 +44,8 @@ class ServerConfig(ctypes.Structure):
 class Request(ctypes.Structure):
     _fields_ = [("a", ctypes.c_double), ("b", ctypes.c_double), ("c", ctypes.c_double), ("d", ctypes.c_double),
                 ("k", ctypes.c_int), ("m", ctypes.c_uint64), ("seed", ctypes.c_uint64),
-                ("table_bound", ctypes.c_uint64), ("flags", ctypes.c_uint)]
+                ("table_bound", ctypes.c_uint64), ("flags", ctypes.c_uint),
+                ("scramble", ctypes.c_int), ("scramble_seed", ctypes.c_uint64)]
 
 
 class RequestStatus(ctypes.Structure):
@@ -77,6 +78,7 @@ SIGNATURES = [
     ("rmat_build_table_fixed", _st, [_dbl, _dbl, _dbl, _dbl, _i32, _i32, _vp]),
     ("rmat_build_table_levels", _st, [_vp, _i32, _i32, _u32, _vp]),
     ("rmat_table_set_flags", _st, [_vp, _u32]),
+    ("rmat_table_set_scramble", _st, [_vp, _i32, _u64]),
     ("rmat_table_info", _st, [_vp, _vp]),
     ("rmat_table_group_info", _st, [_vp, _i32, _vp, _vp, _vp]),
     ("rmat_table_export", _st, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),

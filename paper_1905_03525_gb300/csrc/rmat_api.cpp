@@ -245,6 +245,29 @@ rmat_status rmat_table_set_flags(rmat_table *t, unsigned flags) {
     return RMAT_OK;
 }
 
+rmat_status rmat_table_set_scramble(rmat_table *t, int enable, uint64_t scramble_seed) {
+    clear_error();
+    if (!t) return fail(RMAT_ERR_INVALID_ARGUMENT, "table is NULL");
+    std::lock_guard<std::mutex> lk(t->mu);
+    t->scramble = enable != 0;
+    if (t->scramble) {
+        // SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): add the golden-ratio
+        // increment, then the two xor-shift-multiply steps of its finaliser.
+        uint64_t state = scramble_seed;
+        const uint64_t mask = t->k >= 64 ? ~uint64_t(0) : ((uint64_t(1) << t->k) - 1);
+        for (int i = 0; i < 6; ++i) {
+            state += 0x9E3779B97F4A7C15ull;
+            uint64_t z = state;
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            z ^= z >> 31;
+            t->scr[i] = (i % 2 == 0 ? (z | 1u) : z) & mask;
+        }
+    }
+    t->plans.clear();
+    return RMAT_OK;
+}
+
 rmat_status rmat_table_info(const rmat_table *t, rmat_table_info_t *info) {
     clear_error();
     if (!t || !info) return fail(RMAT_ERR_INVALID_ARGUMENT, "NULL argument");

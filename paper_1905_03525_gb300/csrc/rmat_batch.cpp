@@ -22,6 +22,7 @@ struct Side {
     bool u64 = false;
     void *arena = nullptr;
     rmat::Job *jobs = nullptr;
+    rmat::Scramble *scr = nullptr;
     uint32_t *unit_job = nullptr;
     unsigned long long *counter = nullptr;
     uint64_t units = 0;
@@ -34,6 +35,7 @@ struct Side {
 void free_side(Side &s) {
     if (s.arena) cudaFree(s.arena);
     if (s.jobs) cudaFree(s.jobs);
+    if (s.scr) cudaFree(s.scr);
     if (s.unit_job) cudaFree(s.unit_job);
     if (s.counter) cudaFree(s.counter);
     s = Side{};
@@ -106,7 +108,9 @@ rmat_status prepare_side(rmat_batch *b, bool u64, const DeviceProps &props, Side
 
     const uint64_t unit_edges = uint64_t(threads / 32) * tile * 4;
     std::vector<Job> jobs;
+    std::vector<Scramble> scrs;
     jobs.reserve(mine.size());
+    scrs.reserve(mine.size());
     uint64_t units = 0;
     for (const auto *en : mine) {
         const uint32_t *blob =
@@ -116,6 +120,7 @@ rmat_status prepare_side(rmat_batch *b, bool u64, const DeviceProps &props, Side
         J.unit_begin = units;
         units += (en->count + unit_edges - 1) / unit_edges;
         jobs.push_back(J);
+        scrs.push_back(make_scramble(en->t));
     }
     if (units >= (uint64_t(1) << 40)) return fail(RMAT_ERR_INVALID_ARGUMENT, "batch too large");
     std::vector<uint32_t> unit_job(units);
@@ -124,10 +129,13 @@ rmat_status prepare_side(rmat_batch *b, bool u64, const DeviceProps &props, Side
         std::fill(unit_job.begin() + jobs[j].unit_begin, unit_job.begin() + end, uint32_t(j));
     }
     if (rmat_status st = dev_alloc(&s.jobs, jobs.size() * sizeof(Job))) return st;
+    if (rmat_status st = dev_alloc(&s.scr, scrs.size() * sizeof(Scramble))) return st;
     if (rmat_status st = dev_alloc(&s.unit_job, unit_job.size() * sizeof(uint32_t))) return st;
     if (rmat_status st = dev_alloc(&s.counter, sizeof(unsigned long long))) return st;
     cudaError_t e = cudaMemcpy(s.jobs, jobs.data(), jobs.size() * sizeof(Job), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_err("batch job upload", e);
+    e = cudaMemcpy(s.scr, scrs.data(), scrs.size() * sizeof(Scramble), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_err("batch scramble upload", e);
     e = cudaMemcpy(s.unit_job, unit_job.data(), unit_job.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_err("batch unit upload", e);
 
@@ -141,6 +149,7 @@ rmat_status prepare_side(rmat_batch *b, bool u64, const DeviceProps &props, Side
     s.njobs = jobs.size();
     s.grid = int(std::min<uint64_t>(uint64_t(props.sms) * per_sm, units));
     s.args.jobs = s.jobs;
+    s.args.scr = s.scr;
     s.args.unit_job = s.unit_job;
     s.args.units = units;
     s.args.unit_edges = unit_edges;

@@ -75,6 +75,8 @@ struct rmat_table {
     std::vector<rmat::GroupDesc> gdesc;
     std::mutex mu;
     std::map<int, rmat::DeviceCopy> dev;    // device ordinal -> copy
+    bool scramble = false;                  // relabel vertex IDs
+    uint64_t scr[6] = {0, 0, 0, 0, 0, 0};   // m0, a0, m1, a1, m2, a2
     bool cfg_set = false;
     rmat_launch_config_t cfg{};
     std::map<int, rmat::AliasPlan> plans;   // device ordinal -> launch plan

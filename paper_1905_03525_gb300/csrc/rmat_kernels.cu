@@ -93,10 +93,49 @@ __device__ __forceinline__ void put_pair(uint32_t stage, uint32_t idx, uint64_t 
         dev::sts64(stage + 8u * idx, uint32_t(r), uint32_t(c));
 }
 
-template <bool U64, bool UNDIR>
-__device__ __forceinline__ void put_final(uint32_t stage, uint32_t idx, const typename AccT<U64>::type &acc, int k) {
-    uint64_t r = acc.out_row(k), c = acc.out_col(k);
-    if (UNDIR && r > c) {
+// Vertex relabelling pi (three rounds of x ^= x >> ceil(k/2); x = x*m + a,
+// all mod 2^k), a bijection of [0, 2^k), applied to the accumulator word X
+// that holds x in its top k bits (W-bit word, s = W - k; the bits below may
+// hold levels drawn past k).  With X = x * 2^s: X*m + a*2^s = (x*m + a) * 2^s
+// mod 2^W, and (X >> h) with its bits below 2^s cleared is (x >> h) * 2^s, so
+// the rounds need no reduction mod 2^k.  Returns pi(x), right-aligned.
+template <bool U64>
+__device__ __forceinline__ uint64_t scramble_id(typename AccT<U64>::word X, const Job &J, const Scramble &S) {
+    const uint32_t h = uint32_t(J.k + 1) >> 1;
+    using Word = typename AccT<U64>::word;
+    constexpr uint32_t W = U64 ? 64 : 32;
+    const Word M = Word(S.mask);
+    X &= M;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        X ^= (X >> h) & M;
+        X = X * Word(S.m[i]) + Word(S.a[i]);
+    }
+    return uint64_t(X >> (W - uint32_t(J.k)));
+}
+
+// Store-epilogue variants (template argument EPI): bit 0 mirrors the edge to
+// (min, max); bit 1 relabels every edge; bit 2 relabels when the job's flags
+// ask for it (a batched launch mixes jobs with and without relabelling).
+constexpr int kEpiUndir = 1, kEpiScr = 2, kEpiScrFlag = 4;
+
+template <int EPI>
+__device__ __forceinline__ bool relabel(const Job &J) {
+    return (EPI & kEpiScr) || ((EPI & kEpiScrFlag) && (J.flags & kScrambleFlag));
+}
+
+template <bool U64, int EPI>
+__device__ __forceinline__ void put_final(uint32_t stage, uint32_t idx, const typename AccT<U64>::type &acc,
+                                          const Job &J, const Scramble &S) {
+    uint64_t r, c;
+    if (relabel<EPI>(J)) {
+        r = scramble_id<U64>(acc.row, J, S);
+        c = scramble_id<U64>(acc.col, J, S);
+    } else {
+        r = acc.out_row(J.k);
+        c = acc.out_col(J.k);
+    }
+    if ((EPI & kEpiUndir) && r > c) {
         const uint64_t t = r;
         r = c;
         c = t;
@@ -110,9 +149,9 @@ __device__ __forceinline__ void put_final(uint32_t stage, uint32_t idx, const ty
 // edges go to their output slot; unfinished ones leave their raw accumulators
 // in the same slot, their level count in p_fill, and a bit in the lane's mask
 // (bit i = edge i*32 + lane).
-template <int FMT, bool U64, bool SMEM, bool UNDIR, bool FULL, bool KS>
-__device__ __forceinline__ uint32_t phase1(const Job &J, const dev::Group<SMEM> &G0, uint64_t ebase, uint32_t n,
-                                           uint32_t stage, uint32_t p_fill, int lane) {
+template <int FMT, bool U64, bool SMEM, int EPI, bool FULL, bool KS>
+__device__ __forceinline__ uint32_t phase1(const Job &J, const Scramble &S, const dev::Group<SMEM> &G0,
+                                           uint64_t ebase, uint32_t n, uint32_t stage, uint32_t p_fill, int lane) {
     using Acc = typename AccT<U64>::type;
     const uint32_t uk = uint32_t(J.k);
     uint32_t pm = 0;
@@ -128,7 +167,11 @@ __device__ __forceinline__ uint32_t phase1(const Job &J, const dev::Group<SMEM> 
         const bool done = acc.filled >= uk;
         uint64_t r = done ? acc.out_row(J.k) : uint64_t(acc.row);
         uint64_t c = done ? acc.out_col(J.k) : uint64_t(acc.col);
-        if (UNDIR && done && r > c) {
+        if (relabel<EPI>(J) && done) {
+            r = scramble_id<U64>(acc.row, J, S);
+            c = scramble_id<U64>(acc.col, J, S);
+        }
+        if ((EPI & kEpiUndir) && done && r > c) {
             const uint64_t t = r;
             r = c;
             c = t;
@@ -167,8 +210,8 @@ __device__ __forceinline__ uint32_t phase1(const Job &J, const dev::Group<SMEM> 
 // sgroups: shared address of precomputed group descriptors (uint4 {A, Bs, Ba,
 // 2^b} per group) for per-level tables staged in shared memory, or 0 to read
 // them from the blob header at every draw.
-template <int FMT, bool U64, bool SMEM, bool LEVELS, bool UNDIR, bool KS>
-__device__ __forceinline__ void gen_tile(const Job &J, uint32_t sblob, const uint32_t *gblob,
+template <int FMT, bool U64, bool SMEM, bool LEVELS, int EPI, bool KS>
+__device__ __forceinline__ void gen_tile(const Job &J, const Scramble &S, uint32_t sblob, const uint32_t *gblob,
                                          const dev::Group<SMEM> &G0, uint64_t first, uint32_t n, WarpState &W,
                                          uint32_t sgroups = 0) {
     using Acc = typename AccT<U64>::type;
@@ -211,12 +254,12 @@ __device__ __forceinline__ void gen_tile(const Job &J, uint32_t sblob, const uin
                     }
                 }
             }
-            if (idx < n) put_final<U64, UNDIR>(stage, idx, acc, J.k);
+            if (idx < n) put_final<U64, EPI>(stage, idx, acc, J, S);
         }
     } else {
         const uint32_t pm = n == uint32_t(W.tile)
-                                ? phase1<FMT, U64, SMEM, UNDIR, true, KS>(J, G0, ebase, n, stage, p_fill, lane)
-                                : phase1<FMT, U64, SMEM, UNDIR, false, KS>(J, G0, ebase, n, stage, p_fill, lane);
+                                ? phase1<FMT, U64, SMEM, EPI, true, KS>(J, S, G0, ebase, n, stage, p_fill, lane)
+                                : phase1<FMT, U64, SMEM, EPI, false, KS>(J, S, G0, ebase, n, stage, p_fill, lane);
         // Phase 2: queue the unfinished edges of the whole tile (warp prefix
         // sum of the lanes' counts), then finish them 32 at a time.
         const uint32_t cnt = __popc(pm);
@@ -269,7 +312,7 @@ __device__ __forceinline__ void gen_tile(const Job &J, uint32_t sblob, const uin
                     if (!__any_sync(0xffffffffu, acc.filled < uk)) break;
                     if (!U64 || acc.filled < uk) dev::draw<FMT, SMEM>(G0, w.w, acc);
                 }
-                if (has) put_final<U64, UNDIR>(stage, idx, acc, J.k);
+                if (has) put_final<U64, EPI>(stage, idx, acc, J, S);
             }
         }
     }
@@ -310,8 +353,9 @@ __device__ __forceinline__ bool stage_blob(unsigned char *dst, const uint32_t *s
     return __syncthreads_and(ok) != 0;
 }
 
-template <int FMT, bool U64, bool SMEM, bool LEVELS, bool UNDIR>
-__global__ void __launch_bounds__(1024) k_alias(const __grid_constant__ Job J, int tile, unsigned *err) {
+template <int FMT, bool U64, bool SMEM, bool LEVELS, int EPI>
+__global__ void __launch_bounds__(1024, 1) k_alias(const __grid_constant__ Job J, const __grid_constant__ Scramble S,
+                                                int tile, unsigned *err) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
     // per-level tables in shared memory get 1 KB of precomputed group descriptors
@@ -360,22 +404,22 @@ __global__ void __launch_bounds__(1024) k_alias(const __grid_constant__ Job J, i
         const uint64_t first = t * tile;
         const uint64_t left = J.count - first;
         const uint32_t n = left < uint64_t(tile) ? uint32_t(left) : uint32_t(tile);
-        gen_tile<FMT, U64, SMEM, LEVELS, UNDIR, true>(J, sblob, J.blob, G0, first, n, W, sgroups);
+        gen_tile<FMT, U64, SMEM, LEVELS, EPI, true>(J, S, sblob, J.blob, G0, first, n, W, sgroups);
     }
     if (lane == 0 && W.issued) dev::bulk_wait_all();
 }
 
 // One work unit of a batch: edges [u * unit_edges, ...) of job unit_job[u].
-template <bool U64, int FMT, bool SMEM, bool LEVELS, bool UNDIR>
-__device__ __forceinline__ void batch_unit(const Job &J, uint32_t sblob, uint64_t local_unit, uint64_t unit_edges,
-                                           int nwarps, int warp, WarpState &W) {
+template <bool U64, int FMT, bool SMEM, bool LEVELS, int EPI>
+__device__ __forceinline__ void batch_unit(const Job &J, const Scramble &S, uint32_t sblob, uint64_t local_unit,
+                                           uint64_t unit_edges, int nwarps, int warp, WarpState &W) {
     const dev::Group<SMEM> G0 = group0<SMEM>(J, sblob);
     const uint64_t f0 = local_unit * unit_edges;
     const uint64_t end = min(J.count, f0 + unit_edges);
     for (uint64_t first = f0 + uint64_t(warp) * W.tile; first < end; first += uint64_t(nwarps) * W.tile) {
         const uint64_t left = end - first;
         const uint32_t n = left < uint64_t(W.tile) ? uint32_t(left) : uint32_t(W.tile);
-        gen_tile<FMT, U64, SMEM, LEVELS, UNDIR, false>(J, sblob, J.blob, G0, first, n, W);
+        gen_tile<FMT, U64, SMEM, LEVELS, EPI, false>(J, S, sblob, J.blob, G0, first, n, W);
     }
 }
 
@@ -429,7 +473,8 @@ __global__ void __launch_bounds__(1024) k_batch(BatchArgs B) {
         }
         const uint64_t local = unit - J.unit_begin;
         const int sel = (J.fmt ? 8 : 0) | (J.smem ? 4 : 0) | (J.levels ? 2 : 0) | ((J.flags & RMAT_UNDIRECTED) ? 1 : 0);
-#define RMAT_UNIT(F, S, L, U) batch_unit<U64, F, S, L, U>(J, sblob, local, B.unit_edges, nwarps, warp, W)
+        const Scramble &S = B.scr[jid];  // read (from global memory) only when relabelling
+#define RMAT_UNIT(F, SM, L, U) batch_unit<U64, F, SM, L, (U ? kEpiUndir : 0) | kEpiScrFlag>(J, S, sblob, local, B.unit_edges, nwarps, warp, W)
         switch (sel) {
             case 0: RMAT_UNIT(0, false, false, false); break;
             case 1: RMAT_UNIT(0, false, false, true); break;
@@ -539,17 +584,19 @@ __global__ void __launch_bounds__(256) k_naive(NaiveArgs a) {
     }
 }
 
-template <int FMT, bool U64, bool SMEM, bool LEVELS, bool UNDIR>
+template <int FMT, bool U64, bool SMEM, bool LEVELS, int EPI>
 void *alias_kernel_ptr() {
-    return reinterpret_cast<void *>(&k_alias<FMT, U64, SMEM, LEVELS, UNDIR>);
+    return reinterpret_cast<void *>(&k_alias<FMT, U64, SMEM, LEVELS, EPI>);
 }
 
 using KernelFn = void *(*)();
-#define RMAT_K2(F, U, S, L) {alias_kernel_ptr<F, U, S, L, false>, alias_kernel_ptr<F, U, S, L, true>}
+#define RMAT_K2(F, U, S, L) \
+    {alias_kernel_ptr<F, U, S, L, 0>, alias_kernel_ptr<F, U, S, L, 1>, alias_kernel_ptr<F, U, S, L, 2>, \
+     alias_kernel_ptr<F, U, S, L, 3>}
 #define RMAT_K4(F, U, S) {RMAT_K2(F, U, S, false), RMAT_K2(F, U, S, true)}
 #define RMAT_K8(F, U) {RMAT_K4(F, U, false), RMAT_K4(F, U, true)}
-// [format][u64][shared table][per-level][undirected]
-KernelFn alias_kernel_table[2][2][2][2][2] = {{RMAT_K8(0, false), RMAT_K8(0, true)},
+// [format][u64][shared table][per-level][epilogue: undirected | relabel << 1]
+KernelFn alias_kernel_table[2][2][2][2][4] = {{RMAT_K8(0, false), RMAT_K8(0, true)},
                                               {RMAT_K8(1, false), RMAT_K8(1, true)}};
 #undef RMAT_K8
 #undef RMAT_K4
@@ -663,7 +710,8 @@ rmat_status plan_alias_launch(const rmat_table *t, const rmat_launch_config_t &w
     plan.threads = threads;
     plan.tile = tile;
     plan.smem_bytes = need(smem_table, threads, tile);
-    plan.kernel = alias_kernel_table[plan.fmt][u64][smem_table][levels][(t->flags & RMAT_UNDIRECTED) ? 1 : 0]();
+    plan.kernel = alias_kernel_table[plan.fmt][u64][smem_table][levels]
+                                    [((t->flags & RMAT_UNDIRECTED) ? kEpiUndir : 0) | (t->scramble ? kEpiScr : 0)]();
     cudaError_t e = set_smem_attr(plan.kernel, plan.smem_bytes);
     if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
     int per_sm = 0;
@@ -699,6 +747,7 @@ Job make_job(const rmat_table *t, const uint32_t *dblob, bool smem, uint64_t see
     J.out = out;
     J.fmt = uint32_t(t->format);
     J.smem = smem ? 1u : 0u;
+    if (t->scramble) J.flags |= kScrambleFlag;
     J.a0 = t->gdesc[0].a_off_words;
     J.bs0 = t->gdesc[0].bs_off_words;
     J.ba0 = t->gdesc[0].ba_off_words;
@@ -707,10 +756,25 @@ Job make_job(const rmat_table *t, const uint32_t *dblob, bool smem, uint64_t see
     return J;
 }
 
+Scramble make_scramble(const rmat_table *t) {
+    Scramble S{};
+    if (!t->scramble) return S;
+    const int W = t->k > 32 ? 64 : 32;
+    const int s = W - t->k;
+    const uint64_t wmask = W == 64 ? ~0ull : 0xFFFFFFFFull;
+    for (int i = 0; i < 3; ++i) {
+        S.m[i] = t->scr[2 * i];
+        S.a[i] = (t->scr[2 * i + 1] << s) & wmask;
+    }
+    S.mask = (wmask << s) & wmask;
+    return S;
+}
+
 rmat_status launch_alias(const rmat_table *t, const uint32_t *dblob, const AliasPlan &plan, uint64_t seed,
                          uint64_t e0, uint64_t count, void *out, cudaStream_t stream) {
     if (count == 0) return RMAT_OK;
     Job J = make_job(t, dblob, plan.smem_table, seed, e0, count, out);
+    Scramble S = make_scramble(t);
     unsigned *err = plan.err;
     const int warps = plan.threads / 32;
     // Small launches: smaller tiles (down to 64 edges) until every warp of a
@@ -723,7 +787,7 @@ rmat_status launch_alias(const rmat_table *t, const uint32_t *dblob, const Alias
     const uint64_t want_ctas = (ntiles + warps - 1) / warps;
     const uint64_t max_ctas = uint64_t(plan.sms) * plan.ctas_per_sm;
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want_ctas, max_ctas)));
-    void *params[] = {&J, &tile, &err};
+    void *params[] = {&J, &S, &tile, &err};
     cudaError_t e = cudaLaunchKernel(plan.kernel, dim3(grid), dim3(plan.threads), params, plan.smem_bytes, stream);
     if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     return RMAT_OK;

@@ -37,8 +37,22 @@ struct Job {
     uint64_t unit_begin;   // first work unit of this job (batches)
 };
 
+// Vertex relabelling constants of a job (used when flags & kScrambleFlag),
+// in the form the kernels apply them: to an identifier held left-aligned in a
+// W-bit word (W = 32 for k <= 32, else 64), s = W - k.  m[i] is the round's
+// odd multiplier, a[i] its addend times 2^s (mod 2^W), mask = the top k bits.
+// Kept out of Job so that the batched kernel's register copy of a job stays
+// small.
+struct Scramble {
+    uint64_t m[3], a[3], mask;
+};
+
+// Job flag (beside RMAT_UNDIRECTED): relabel vertex IDs with Job::scr.
+constexpr unsigned kScrambleFlag = 0x100u;
+
 struct BatchArgs {
     const Job *jobs;
+    const Scramble *scr;       // one per job
     const uint32_t *unit_job;  // job of every work unit
     uint64_t units;
     uint64_t unit_edges;
@@ -53,6 +67,7 @@ rmat_launch_config_t default_launch_config(const rmat_table *t);
 rmat_status plan_alias_launch(const rmat_table *t, const rmat_launch_config_t &want, AliasPlan &plan);
 Job make_job(const rmat_table *t, const uint32_t *dblob, bool smem, uint64_t seed, uint64_t e0, uint64_t count,
              void *out);
+Scramble make_scramble(const rmat_table *t);
 rmat_status launch_alias(const rmat_table *t, const uint32_t *dblob, const AliasPlan &plan, uint64_t seed,
                          uint64_t e0, uint64_t count, void *out, cudaStream_t stream);
 size_t warp_bytes(bool u64, bool levels, int tile);

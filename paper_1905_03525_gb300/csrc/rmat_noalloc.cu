@@ -96,11 +96,12 @@ extern "C" rmat_status rmat_generate_batch_noalloc(const rmat_table *const *tabl
     const size_t budget = size_t(props.max_smem) - 16 - size_t(threads / 32) * per_warp;
     const uint64_t unit_edges = uint64_t(threads / 32) * tile * 4;
 
-    // Scratch layout: [counter][jobs][unit -> job][table blobs].
+    // Scratch layout: [counter][jobs][relabelling constants][unit -> job][table blobs].
     uint64_t units = 0;
     for (uint32_t i = 0; i < n; ++i) units += (counts[i] + unit_edges - 1) / unit_edges;
     const size_t off_jobs = 256;
-    const size_t off_units = align256(off_jobs + sizeof(Job) * n);
+    const size_t off_scr = align256(off_jobs + sizeof(Job) * n);
+    const size_t off_units = align256(off_scr + sizeof(Scramble) * n);
     size_t off_blobs = align256(off_units + sizeof(uint32_t) * units);
     if (units > RMAT_NOALLOC_SCRATCH_BYTES / 4 || off_blobs > RMAT_NOALLOC_SCRATCH_BYTES)
         return fail(RMAT_ERR_INVALID_ARGUMENT, "too many edges for the no-alloc scratch");
@@ -123,6 +124,7 @@ extern "C" rmat_status rmat_generate_batch_noalloc(const rmat_table *const *tabl
     // counter starts at zero (the launch below also clears it on the stream).
     std::memset(g_host_image, 0, off_blobs);
     Job *jobs = reinterpret_cast<Job *>(g_host_image + off_jobs);
+    Scramble *scrs = reinterpret_cast<Scramble *>(g_host_image + off_scr);
     uint32_t *unit_job = reinterpret_cast<uint32_t *>(g_host_image + off_units);
     uint64_t u = 0;
     for (uint32_t i = 0; i < n; ++i) {
@@ -131,6 +133,7 @@ extern "C" rmat_status rmat_generate_batch_noalloc(const rmat_table *const *tabl
         const bool smem = t->image.size() * 4 <= budget;
         jobs[i] = make_job(t, dblob, smem, seeds[i], edge_offsets[i], counts[i], outs[i]);
         jobs[i].unit_begin = u;
+        scrs[i] = make_scramble(t);
         const uint64_t nu = (counts[i] + unit_edges - 1) / unit_edges;
         for (uint64_t k = 0; k < nu; ++k) unit_job[u + k] = i;
         u += nu;
@@ -149,6 +152,7 @@ extern "C" rmat_status rmat_generate_batch_noalloc(const rmat_table *const *tabl
     if (per_sm < 1) return fail(RMAT_ERR_UNSUPPORTED, "launch shape does not fit on an SM");
     BatchArgs args{};
     args.jobs = reinterpret_cast<const Job *>(scratch + off_jobs);
+    args.scr = reinterpret_cast<const Scramble *>(scratch + off_scr);
     args.unit_job = reinterpret_cast<const uint32_t *>(scratch + off_units);
     args.units = units;
     args.unit_edges = unit_edges;

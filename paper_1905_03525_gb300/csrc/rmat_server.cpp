@@ -114,9 +114,11 @@ struct rmat_server {
     unsigned char *arena_dev = nullptr;
     rmat::Arena *arena = nullptr;
     rmat::Job *d_jobs = nullptr;
+    rmat::Scramble *d_scr = nullptr;
     uint32_t *d_units = nullptr;
     unsigned long long *d_counter = nullptr, *d_sums = nullptr;
     rmat::Job *h_jobs = nullptr;       // pinned staging
+    rmat::Scramble *h_scr = nullptr;
     uint32_t *h_units = nullptr;
     unsigned long long *h_sums = nullptr;
     uint64_t max_units = 0;
@@ -217,14 +219,18 @@ rmat_status run_step(rmat_server *s, const std::vector<Request *> &picked, const
         for (uint64_t k = 0; k < nu; ++k) s->h_units[units + k] = uint32_t(j);
         units += nu;
         s->h_jobs[j] = J;
+        s->h_scr[j] = make_scramble(r->table);
     }
     cudaError_t e;
     if ((e = cudaMemcpyAsync(s->d_jobs, s->h_jobs, picked.size() * sizeof(Job), cudaMemcpyHostToDevice, s->stream)) ||
+        (e = cudaMemcpyAsync(s->d_scr, s->h_scr, picked.size() * sizeof(Scramble), cudaMemcpyHostToDevice,
+                             s->stream)) ||
         (e = cudaMemcpyAsync(s->d_units, s->h_units, units * sizeof(uint32_t), cudaMemcpyHostToDevice, s->stream)) ||
         (e = cudaMemsetAsync(s->d_sums, 0, picked.size() * sizeof(unsigned long long), s->stream)))
         return fail(RMAT_ERR_CUDA, std::string("server upload: ") + cudaGetErrorString(e));
     BatchArgs a{};
     a.jobs = s->d_jobs;
+    a.scr = s->d_scr;
     a.unit_job = s->d_units;
     a.units = units;
     a.unit_edges = ue;
@@ -336,10 +342,12 @@ void free_server(rmat_server *s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     if (s->arena_dev) cudaFree(s->arena_dev);
     if (s->d_jobs) cudaFree(s->d_jobs);
+    if (s->d_scr) cudaFree(s->d_scr);
     if (s->d_units) cudaFree(s->d_units);
     if (s->d_counter) cudaFree(s->d_counter);
     if (s->d_sums) cudaFree(s->d_sums);
     if (s->h_jobs) cudaFreeHost(s->h_jobs);
+    if (s->h_scr) cudaFreeHost(s->h_scr);
     if (s->h_units) cudaFreeHost(s->h_units);
     if (s->h_sums) cudaFreeHost(s->h_sums);
     if (s->stream) cudaStreamDestroy(s->stream);
@@ -391,10 +399,12 @@ rmat_status rmat_server_create(const rmat_server_config_t *cfg, rmat_server **ou
     // step_edges / unit_edges + max_active units.
     s->max_units = cfg->step_edges / unit_edges_for(true) + uint64_t(cfg->max_active) + 1;
     if (st == RMAT_OK) st = dev_alloc(&s->d_jobs, sizeof(Job) * cfg->max_active);
+    if (st == RMAT_OK) st = dev_alloc(&s->d_scr, sizeof(Scramble) * cfg->max_active);
     if (st == RMAT_OK) st = dev_alloc(&s->d_units, sizeof(uint32_t) * s->max_units);
     if (st == RMAT_OK) st = dev_alloc(&s->d_counter, sizeof(unsigned long long));
     if (st == RMAT_OK) st = dev_alloc(&s->d_sums, sizeof(unsigned long long) * cfg->max_active);
     if (st == RMAT_OK) st = host_alloc(&s->h_jobs, sizeof(Job) * cfg->max_active);
+    if (st == RMAT_OK) st = host_alloc(&s->h_scr, sizeof(Scramble) * cfg->max_active);
     if (st == RMAT_OK) st = host_alloc(&s->h_units, sizeof(uint32_t) * s->max_units);
     if (st == RMAT_OK) st = host_alloc(&s->h_sums, sizeof(unsigned long long) * cfg->max_active);
     if (st != RMAT_OK) {
@@ -437,6 +447,10 @@ rmat_status rmat_server_submit(rmat_server *s, const rmat_request_t *req, uint64
         bound /= 2;
     }
     if (rmat_status st = rmat_table_set_flags(t, req->flags)) {
+        rmat_free_table(t);
+        return st;
+    }
+    if (rmat_status st = rmat_table_set_scramble(t, req->scramble, req->scramble_seed)) {
         rmat_free_table(t);
         return st;
     }

@@ -38,8 +38,11 @@ class Server:
         self._cb = CHUNK_FN(lambda user, rid, off, cnt, ptr: fn(rid, off, cnt, ptr))
         check(lib().rmat_server_set_chunk_callback(self._h, self._cb, None))
 
-    def submit(self, a, b, c, d, k, m, seed, table_bound=0, flags=0) -> int:
-        req = Request(a, b, c, d, k, m, seed, table_bound, flags)
+    def submit(self, a, b, c, d, k, m, seed, table_bound=0, flags=0, scramble_seed=None) -> int:
+        """Queue edges 0..m-1 of one graph; scramble_seed (not None) relabels
+        its vertices as rmat_table_set_scramble does."""
+        req = Request(a, b, c, d, k, m, seed, table_bound, flags, int(scramble_seed is not None),
+                      scramble_seed or 0)
         rid = ctypes.c_uint64()
         check(lib().rmat_server_submit(self._h, ctypes.byref(req), ctypes.byref(rid)))
         return rid.value

@@ -104,3 +104,21 @@ def test_batch_in_cuda_graph():
         rm.rmat_generate(t, seed, e0, m, ref)
         torch.cuda.synchronize()
         assert torch.equal(out, ref)
+
+
+def test_batch_scrambled_graphs_match_single_launches():
+    jobs = _mixed_jobs()[:12] + _mixed_jobs()[-5:-2]
+    b = rm.rmat_batch_create()
+    outs = []
+    for i, (t, k, seed, e0, m) in enumerate(jobs):
+        rm.rmat_table_set_scramble(t, i % 2 == 0, 1000 + i)
+        out = rm.empty_edges(m, k)
+        rm.rmat_batch_add(b, t, seed, e0, m, out)
+        outs.append(out)
+    rm.rmat_batch_launch(b)
+    torch.cuda.synchronize()
+    for (t, k, seed, e0, m), out in zip(jobs, outs):
+        ref = rm.empty_edges(m, k)
+        rm.rmat_generate(t, seed, e0, m, ref)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)

@@ -242,3 +242,25 @@ def test_tables_with_different_shared_memory_needs_interleave():
         if name not in refs:
             refs[name] = oracle.generate([oracle.Table.variable(*G500, k, bound)], k, 9, 0, m)
         assert_same(got, refs[name])
+
+
+@pytest.mark.parametrize("kind,k,undirected", [("variable", 26, False), ("variable", 26, True), ("fixed", 16, False),
+                                               ("variable", 40, True), ("levels", 34, True), ("variable", 32, False)])
+def test_scrambled_ids_match_oracle(kind, k, undirected):
+    m = 30_000
+    if kind == "variable":
+        t = rm.rmat_build_table(*G500, k, 4096)
+        ot = [oracle.Table.variable(*G500, k, 4096)]
+    elif kind == "fixed":
+        t = rm.rmat_build_table_fixed(*ASYM, k, 4)
+        ot = [oracle.Table.fixed([ASYM], 4)]
+    else:
+        P = noisy_levels(k, seed=5)
+        t = rm.rmat_build_table_levels(P, k, 6)
+        ot = oracle.level_groups(P, k, 6)
+    rm.rmat_table_set_flags(t, rm.RMAT_UNDIRECTED if undirected else 0)
+    rm.rmat_table_set_scramble(t, True, 2024 + k)
+    ref = oracle.generate_scrambled(ot, k, 2024 + k, 77, 5, m, undirected=undirected)
+    assert_same(gpu_edges(t, k, 77, 5, m), ref)
+    rm.rmat_table_set_scramble(t, False)
+    assert_same(gpu_edges(t, k, 77, 5, m), oracle.generate(ot, k, 77, 5, m, undirected=undirected))

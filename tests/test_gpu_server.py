@@ -147,3 +147,20 @@ def test_rejections_and_timeouts():
             srv.wait(rid, 0.0005)
         assert ei.value.status == _capi.RMAT_ERR_TIMEOUT
         assert srv.wait(rid, 600)["state"] == DONE
+
+
+def test_scrambled_request_matches_scrambled_table():
+    p, k, m, s = SKEWED, 26, 300_001, 2
+    with Server(128 << 20, chunk_edges=1 << 16, step_edges=1 << 18, max_active=2) as srv:
+        plain = srv.submit(*p, k, m, s)
+        scr = srv.submit(*p, k, m, s, scramble_seed=4242)
+        srv.drain(600)
+        a, b = srv.status(plain), srv.status(scr)
+    assert a["state"] == DONE and b["state"] == DONE and a["checksum"] != b["checksum"]
+    t = rm.rmat_build_table(*p, k, b["table_bound"])
+    rm.rmat_table_set_scramble(t, True, 4242)
+    out = rm.empty_edges(m, k)
+    rm.rmat_generate(t, s, 0, m, out)
+    torch.cuda.synchronize()
+    h = out.cpu().numpy().view(np.uint32)
+    assert b["checksum"] == host_checksum(h[:, 0].astype(np.uint64), h[:, 1].astype(np.uint64), 0)

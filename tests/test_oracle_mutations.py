@@ -35,9 +35,14 @@ MUTATIONS = [
     ("naive sampler uses a+c for the second threshold", "T[3 * lvl + 1] = naive_threshold(P[0] + P[1]);",
      "T[3 * lvl + 1] = naive_threshold(P[0] + P[2]);",
      [lambda: pins.test_per_level_quadrant_frequencies("naive")]),
-    ("undirected keeps the larger index first", "if (undirected && r > c) { uint64_t tmp = r; r = c; c = tmp; }\n        row[i] = r;\n        col[i] = c;\n    }\n    return 0;\n}\n\n/* Threshold",
-     "if (undirected && r < c) { uint64_t tmp = r; r = c; c = tmp; }\n        row[i] = r;\n        col[i] = c;\n    }\n    return 0;\n}\n\n/* Threshold",
+    ("undirected keeps the larger index first", "            c = orc_scramble(c, k, consts);\n        }\n        if (undirected && r > c)",
+     "            c = orc_scramble(c, k, consts);\n        }\n        if (undirected && r < c)",
      [pins.test_undirected_mirrors_lower_triangle]),
+    ("scramble shift loses a bit", "int h = (k + 1) / 2;", "int h = k / 2;",
+     [lambda: pins.test_scramble_is_a_bijection(1, 3)]),
+    ("scramble multiplier may be even", "out[2 * i] = (splitmix64_next(&st) | 1ull) & mask;",
+     "out[2 * i] = splitmix64_next(&st) & mask;",
+     [lambda: pins.test_scramble_is_a_bijection(12, 7), lambda: pins.test_scramble_is_a_bijection(16, 123456789)]),
 ]
 
 

@@ -415,3 +415,42 @@ def test_draw_keeps_column_with_probability_thr_over_C_exactly():
         else:
             assert keep == int(t.thr[j])
             assert all(s == t.alias[j] for s in sel[int(t.thr[j]):])
+
+
+# ------------------------------------------------------------ scrambling --
+
+@pytest.mark.parametrize("k,seed", [(1, 3), (2, 9), (5, 1), (12, 7), (16, 123456789)])
+def test_scramble_is_a_bijection(k, seed):
+    c = oracle.scramble_constants(seed, k)
+    assert all(int(x) & 1 for x in c[0::2])            # multipliers odd
+    assert all(int(x) < (1 << k) for x in c)
+    imgs = [oracle.scramble(x, k, c) for x in range(1 << k)]
+    assert sorted(imgs) == list(range(1 << k))
+    if k >= 5:
+        assert sum(1 for x, y in zip(range(1 << k), imgs) if x != y) > (1 << k) // 2
+
+
+def test_scramble_relabels_vertices_only():
+    """Scrambling is a relabelling: the scrambled graph has exactly the edges
+    (pi(r), pi(c)) of the plain one, so its degree multiset is unchanged and
+    its edge distribution is the Kronecker distribution moved by pi."""
+    k, m = 6, 1 << 18
+    t = oracle.Table.variable(*ASYM, k, 500)
+    r0, c0 = oracle.generate([t], k, 31, 0, m)
+    rs, cs = oracle.generate_scrambled([t], k, 99, 31, 0, m)
+    consts = oracle.scramble_constants(99, k)
+    pi = np.array([oracle.scramble(x, k, consts) for x in range(1 << k)], np.uint64)
+    assert np.array_equal(rs, pi[r0.astype(np.int64)]) and np.array_equal(cs, pi[c0.astype(np.int64)])
+    deg0 = np.sort(np.bincount(r0.astype(np.int64), minlength=1 << k))
+    degs = np.sort(np.bincount(rs.astype(np.int64), minlength=1 << k))
+    assert np.array_equal(deg0, degs)
+    K = kronecker(ASYM, k)
+    moved = np.zeros_like(K)
+    moved[np.ix_(pi.astype(np.int64), pi.astype(np.int64))] = K
+    counts = np.bincount((rs.astype(np.int64) << k) | cs.astype(np.int64), minlength=1 << (2 * k)).astype(float)
+    probs = moved.ravel()
+    order = np.argsort(probs)
+    small = np.cumsum(probs[order] * m) < 50
+    cc = np.concatenate([[counts[order][small].sum()], counts[order][~small]])
+    pp = np.concatenate([[probs[order][small].sum()], probs[order][~small]])
+    assert _chi2_pvalue(cc, pp) > 1e-3

@@ -73,6 +73,17 @@ def test_noalloc_matches_rmat_generate_twice():
     rm.rmat_check_device_errors()
 
 
+def test_noalloc_scrambled_graphs():
+    tabs = [rm.rmat_build_table(*G500, 26, 4096), rm.rmat_build_table(*SKEWED, 20, 1024)]
+    rm.rmat_table_set_scramble(tabs[0], True, 9)
+    counts = [100_003, 40_000]
+    outs = [rm.empty_edges(m, k) for m, k in zip(counts, (26, 20))]
+    _call_through_c_abi(tabs, [1, 2], [0, 5], counts, outs)
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0], _reference(tabs[0], 1, 0, counts[0], 26))
+    assert torch.equal(outs[1], _reference(tabs[1], 2, 5, counts[1], 20))
+
+
 def test_noalloc_rejects_what_does_not_fit():
     t = rm.rmat_build_table(*G500, 26, 4096)
     big = 1 << 40   # needs far more unit entries than the scratch holds

@@ -6,9 +6,10 @@ never imports this module, and this module never imports the product package.
 
 The C source (``rmat_oracle.c``) restates the paper's table construction
 (Sec. 2, table-construction fragment), Walker's alias method (Sec. 2), the
-sampling loop (Sec. 2, sampling-loop fragment), undirected mirroring (Sec. 3)
-and the naive per-bit R-MAT process (Sec. 1), plus Philox4x32-10 (Salmon et
-al., SC'11).  This file only compiles it with gcc and marshals arguments.
+sampling loop (Sec. 2, sampling-loop fragment), undirected mirroring,
+scrambling and partitioned graphs (Sec. 3) and the naive per-bit R-MAT
+process (Sec. 1), plus Philox4x32-10 (Salmon et al., SC'11) and binomial
+sampling (inversion; BTRS, Hoermann 1993).  This file only compiles it with gcc and marshals arguments.
 """
 from __future__ import annotations
 
@@ -88,6 +89,14 @@ def _declare(L):
     L.orc_scramble.restype = u64
     L.orc_generate_scrambled.argtypes = [vp, i32, i32, i32, vp, u64, u64, u64, vp, vp]
     L.orc_generate_scrambled.restype = i32
+    L.orc_partition_word.argtypes = [u64, i32, u64, i32, u64]
+    L.orc_partition_word.restype = u32
+    L.orc_binomial.argtypes = [u64, dbl, u64, i32, u64, i32]
+    L.orc_binomial.restype = u64
+    L.orc_partition.argtypes = [dbl, dbl, dbl, dbl, i32, u64, u64, u64, u64, u64, vp, vp, vp, vp]
+    L.orc_partition.restype = ctypes.c_int64
+    L.orc_generate_tile.argtypes = [vp, i32, i32, u64, u64, u64, u64, u64, vp, vp]
+    L.orc_generate_tile.restype = i32
 
 
 def _ptr(a: np.ndarray):
@@ -191,6 +200,53 @@ def generate_scrambled(tables, k, scramble_seed, seed, e0, count, undirected=Fal
     if rc != 0:
         raise ValueError("oracle rejected the generate arguments")
     return row, col
+
+
+def partition_word(seed, depth, node, j, n) -> int:
+    return int(lib().orc_partition_word(seed, depth, node, j, n))
+
+
+def binomial(n, p, seed, depth, node, j) -> int:
+    return int(lib().orc_binomial(n, p, seed, depth, node, j))
+
+
+def partition(abcd, t, m, seed, row_tile_begin=0, row_tile_end=None):
+    """Non-empty tiles of a depth-t partition meeting the tile rows
+    [row_tile_begin, row_tile_end): dict of uint64 arrays row, col, count,
+    first (quadtree order)."""
+    if row_tile_end is None:
+        row_tile_end = 1 << t
+    L = lib()
+    n = L.orc_partition(*abcd, t, m, seed, row_tile_begin, row_tile_end, 0, None, None, None, None)
+    if n < 0:
+        raise ValueError("oracle rejected the partition arguments")
+    out = {f: np.zeros(max(n, 1), np.uint64) for f in ("row", "col", "count", "first")}
+    n2 = L.orc_partition(*abcd, t, m, seed, row_tile_begin, row_tile_end, n, _ptr(out["row"]), _ptr(out["col"]),
+                         _ptr(out["count"]), _ptr(out["first"]))
+    assert n2 == n
+    return {f: a[:n] for f, a in out.items()}
+
+
+def generate_tile(table, k, t, tile_row, tile_col, seed, first, count):
+    row = np.zeros(count, np.uint64)
+    col = np.zeros(count, np.uint64)
+    rc = lib().orc_generate_tile(table._h, k, t, tile_row, tile_col, seed, first, count, _ptr(row), _ptr(col))
+    if rc != 0:
+        raise ValueError("oracle rejected the tile arguments")
+    return row, col
+
+
+def generate_partitioned(table, abcd, k, t, m, seed, row_tile_begin=0, row_tile_end=None):
+    """The tiles of partition() and their edges, concatenated in tile order."""
+    tiles = partition(abcd, t, m, seed, row_tile_begin, row_tile_end)
+    rows, cols = [], []
+    for R, C, n, f in zip(tiles["row"], tiles["col"], tiles["count"], tiles["first"]):
+        r, c = generate_tile(table, k, t, int(R), int(C), seed, int(f), int(n))
+        rows.append(r)
+        cols.append(c)
+    if not rows:
+        return tiles, (np.zeros(0, np.uint64), np.zeros(0, np.uint64))
+    return tiles, (np.concatenate(rows), np.concatenate(cols))
 
 
 def generate_naive(P_levels, k, seed, e0, count, undirected=False):

@@ -396,20 +396,23 @@ uint64_t orc_scramble(uint64_t x, int k, const uint64_t c[6])
     return x;
 }
 
-int orc_generate_scrambled(const orc_table *const *tables, int ngroups, int k, int undirected,
-                           const uint64_t *consts, uint64_t seed, uint64_t e0, uint64_t count,
-                           uint64_t *row, uint64_t *col)
+/* The sampling loop.  The edge starts with pre_len levels already fixed
+ * (row and column prefixes pre_r, pre_c: the tile of a partitioned graph;
+ * pre_len = 0 for a whole graph) and draws the remaining levels. */
+static int gen_core(const orc_table *const *tables, int ngroups, int k, int undirected,
+                    const uint64_t *consts, uint64_t seed, uint64_t e0, uint64_t count,
+                    uint64_t pre_r, uint64_t pre_c, int pre_len, uint64_t *row, uint64_t *col)
 {
-    if (ngroups < 1 || k < 1 || k > 64) return -1;
+    if (ngroups < 1 || k < 1 || k > 64 || pre_len < 0 || pre_len > k) return -1;
     if (ngroups > 1) {
         int sum = 0;
         for (int g = 0; g < ngroups; ++g) sum += tables[g]->max_len;
-        if (sum != k) return -1;
+        if (sum != k || pre_len != 0) return -1;
     }
     for (uint64_t i = 0; i < count; ++i) {
         uint64_t e = e0 + i;
-        uint64_t r = 0, c = 0;
-        int filled = 0;
+        uint64_t r = pre_r, c = pre_c;
+        int filled = pre_len;
         uint64_t n = 0;
         while (filled < k) {
             const orc_table *t = tables[ngroups > 1 ? n : 0];
@@ -436,10 +439,182 @@ int orc_generate_scrambled(const orc_table *const *tables, int ngroups, int k, i
     return 0;
 }
 
+int orc_generate_scrambled(const orc_table *const *tables, int ngroups, int k, int undirected,
+                           const uint64_t *consts, uint64_t seed, uint64_t e0, uint64_t count,
+                           uint64_t *row, uint64_t *col)
+{
+    return gen_core(tables, ngroups, k, undirected, consts, seed, e0, count, 0, 0, 0, row, col);
+}
+
 int orc_generate(const orc_table *const *tables, int ngroups, int k, int undirected,
                  uint64_t seed, uint64_t e0, uint64_t count, uint64_t *row, uint64_t *col)
 {
     return orc_generate_scrambled(tables, ngroups, k, undirected, NULL, seed, e0, count, row, col);
+}
+
+/* ------------------------------------------------------------------ */
+/* Partitioned graphs (Sec. 3, communication-free generation of       */
+/* partitioned graphs): a divide-and-conquer pass gives the number of */
+/* edges in each of the 2^t x 2^t tiles of the adjacency matrix, then */
+/* the sampling loop fills each tile's lower k - t levels.             */
+/* ------------------------------------------------------------------ */
+
+/* Word n of the stream of binomial j (0, 1, 2) at recursion node `node`
+ * (= R * 2^depth + C) of depth `depth`.  Counter word 1 has its top bit set:
+ * an edge's stream has the high half of its block index there, which is 0. */
+uint32_t orc_partition_word(uint64_t seed, int depth, uint64_t node, int j, uint64_t n)
+{
+    uint32_t ctr[4] = {(uint32_t)(n / 4), 0x80000000u | ((uint32_t)j << 8) | (uint32_t)depth,
+                       (uint32_t)node, (uint32_t)(node >> 32)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return out[n % 4];
+}
+
+typedef struct {
+    uint64_t seed, node, n;
+    int depth, j;
+} ustream;
+
+/* Uniform in (0, 1) from two words: x = 26 + 26 high bits, (x + 1/2) / 2^52
+ * (exact in FP64). */
+static double next_uniform(ustream *s)
+{
+    uint32_t w0 = orc_partition_word(s->seed, s->depth, s->node, s->j, s->n++);
+    uint32_t w1 = orc_partition_word(s->seed, s->depth, s->node, s->j, s->n++);
+    double x = (double)(w0 >> 6) * 67108864.0 + (double)(w1 >> 6);
+    return (x + 0.5) * 0x1p-52;
+}
+
+/* Inversion by sequential search (n p < 10, p <= 1/2): walk the pmf from 0,
+ * f(x) = f(x-1) * ((n+1) s / x - s) with s = p/q; a uniform that outruns the
+ * rounded pmf restarts with a fresh uniform. */
+static uint64_t binomial_inversion(uint64_t n, double p, ustream *s)
+{
+    const double q = 1.0 - p, sr = p / q, a = ((double)n + 1.0) * sr, f0 = pow(q, (double)n);
+    for (;;) {
+        double u = next_uniform(s), f = f0;
+        uint64_t x = 0;
+        while (u > f) {
+            u -= f;
+            x++;
+            if (x > n) break;
+            f *= a / (double)x - sr;
+        }
+        if (x <= n) return x;
+    }
+}
+
+/* BTRS, transformed rejection with squeeze (W. Hoermann, "The generation of
+ * binomial random variates", J. Statist. Comput. Simul. 46, 1993), for
+ * n p >= 10, p <= 1/2.  The final test compares with the exact log pmf. */
+static uint64_t binomial_btrs(uint64_t n, double p, ustream *s)
+{
+    const double q = 1.0 - p, nd = (double)n;
+    const double spq = sqrt(nd * p * q);
+    const double b = 1.15 + 2.53 * spq;
+    const double a = -0.0873 + 0.0248 * b + 0.01 * p;
+    const double c = nd * p + 0.5;
+    const double vr = 0.92 - 4.2 / b;
+    const double alpha = (2.83 + 5.1 / b) * spq;
+    const double lpq = log(p / q);
+    const double m = floor((nd + 1.0) * p);
+    const double h = lgamma(m + 1.0) + lgamma(nd - m + 1.0);
+    for (;;) {
+        const double u = next_uniform(s) - 0.5;
+        double v = next_uniform(s);
+        const double us = 0.5 - fabs(u);
+        const double x = floor((2.0 * a / us + b) * u + c);
+        if (x < 0.0 || x > nd) continue;
+        if (us >= 0.07 && v <= vr) return (uint64_t)x;
+        v = log(v * alpha / (a / (us * us) + b));
+        if (v <= h - lgamma(x + 1.0) - lgamma(nd - x + 1.0) + (x - m) * lpq) return (uint64_t)x;
+    }
+}
+
+uint64_t orc_binomial(uint64_t n, double p, uint64_t seed, int depth, uint64_t node, int j)
+{
+    ustream s = {seed, node, 0, depth, j};
+    if (n == 0 || !(p > 0.0)) return 0;
+    if (p >= 1.0) return n;
+    const int flip = p > 0.5;
+    const double pp = flip ? 1.0 - p : p;
+    const uint64_t x = (double)n * pp < 10.0 ? binomial_inversion(n, pp, &s) : binomial_btrs(n, pp, &s);
+    return flip ? n - x : x;
+}
+
+typedef struct {
+    double P[4];
+    int t;
+    uint64_t seed, r0, r1, next, n, cap;
+    uint64_t *tr, *tc, *cnt, *first;
+} part_ctx;
+
+/* Node (depth, R, C) holds `count` edges.  Nodes outside the tile rows
+ * [r0, r1) are not split; their edges only advance the edge numbering. */
+static void part_rec(part_ctx *x, int depth, uint64_t R, uint64_t C, uint64_t count)
+{
+    if (count == 0) return;
+    const int below = x->t - depth;
+    const uint64_t lo = R << below, hi = (R + 1) << below;
+    if (hi <= x->r0 || lo >= x->r1) {
+        x->next += count;
+        return;
+    }
+    if (below == 0) {
+        if (x->n < x->cap) {
+            x->tr[x->n] = R;
+            x->tc[x->n] = C;
+            x->cnt[x->n] = count;
+            x->first[x->n] = x->next;
+        }
+        x->n++;
+        x->next += count;
+        return;
+    }
+    const uint64_t node = (R << depth) | C;
+    const double *P = x->P;
+    const double den_b = (P[1] + P[2]) + P[3], den_c = P[2] + P[3];
+    const uint64_t na = orc_binomial(count, P[0], x->seed, depth, node, 0);
+    const uint64_t nb = orc_binomial(count - na, den_b > 0.0 ? P[1] / den_b : 0.0, x->seed, depth, node, 1);
+    const uint64_t nc = orc_binomial(count - na - nb, den_c > 0.0 ? P[2] / den_c : 0.0, x->seed, depth, node, 2);
+    const uint64_t nd = count - na - nb - nc;
+    part_rec(x, depth + 1, 2 * R, 2 * C, na);          /* a: upper left  */
+    part_rec(x, depth + 1, 2 * R, 2 * C + 1, nb);      /* b: upper right */
+    part_rec(x, depth + 1, 2 * R + 1, 2 * C, nc);      /* c: lower left  */
+    part_rec(x, depth + 1, 2 * R + 1, 2 * C + 1, nd);  /* d: lower right */
+}
+
+int64_t orc_partition(double a, double b, double c, double d, int t, uint64_t m, uint64_t seed,
+                      uint64_t row_tile_begin, uint64_t row_tile_end, uint64_t cap,
+                      uint64_t *tile_row, uint64_t *tile_col, uint64_t *count, uint64_t *first)
+{
+    part_ctx x;
+    const double in[4] = {a, b, c, d};
+    if (t < 0 || t > 30 || normalise(in, x.P) != 0) return -1;
+    if (row_tile_begin > row_tile_end || row_tile_end > ((uint64_t)1 << t)) return -1;
+    if (cap && (!tile_row || !tile_col || !count || !first)) return -1;
+    x.t = t;
+    x.seed = seed;
+    x.r0 = row_tile_begin;
+    x.r1 = row_tile_end;
+    x.next = 0;
+    x.n = 0;
+    x.cap = cap;
+    x.tr = tile_row;
+    x.tc = tile_col;
+    x.cnt = count;
+    x.first = first;
+    part_rec(&x, 0, 0, 0, m);
+    return (int64_t)x.n;
+}
+
+int orc_generate_tile(const orc_table *table, int k, int t, uint64_t tile_row, uint64_t tile_col,
+                      uint64_t seed, uint64_t first, uint64_t count, uint64_t *row, uint64_t *col)
+{
+    if (t < 0 || t > k || (t < 64 && (tile_row >> t || tile_col >> t))) return -1;
+    return gen_core(&table, 1, k, 0, NULL, seed, first, count, tile_row, tile_col, t, row, col);
 }
 
 /* Threshold round(x 2^32), saturated to 2^32 - 1. */

@@ -17,6 +17,10 @@
  *   - undirected mirroring (min, max)                               [Sec. 3]
  *   - the naive per-bit R-MAT process (k quadrant draws per edge)   [Sec. 1]
  *   - exact edge distribution implied by a table, by enumeration    [Sec. 1 definition, for pins]
+ *   - scrambling: seeded bijective relabelling of vertex IDs        [Sec. 3]
+ *   - partitioned graphs: divide-and-conquer tile edge counts by    [Sec. 3]
+ *     binomial splits (inversion; BTRS, Hoermann 1993), then the
+ *     sampling loop inside each tile
  *
  * Conventions: symbol s = 2*rowbit + colbit, a->0, b->1, c->2, d->3 (Sec. 1:
  * a = upper-left, b = upper-right, c = lower-left, d = lower-right; the
@@ -86,6 +90,31 @@ uint64_t orc_scramble(uint64_t x, int k, const uint64_t consts[6]);
 int orc_generate_scrambled(const orc_table *const *tables, int ngroups, int k, int undirected,
                            const uint64_t *consts, uint64_t seed, uint64_t e0, uint64_t count,
                            uint64_t *row, uint64_t *col);
+
+/* Partitioned graphs (Sec. 3).  The 2^k x 2^k adjacency matrix is cut into
+ * 2^t x 2^t tiles.  From the root (depth 0, m edges) every node (depth, R, C)
+ * splits its edges among its quadrants a, b, c, d by three binomials:
+ * n_a ~ Bin(n, a), n_b ~ Bin(n - n_a, b/(b+c+d)), n_c ~ Bin(n - n_a - n_b,
+ * c/(c+d)), n_d = the rest; binomial j draws from the stream
+ * orc_partition_word(seed, depth, R * 2^depth + C, j, .).  Tiles (depth t)
+ * are listed in quadtree order (a, b, c, d at every level); the edges of a
+ * tile are numbered consecutively from the count of all edges before it in
+ * that order, and edge e of tile (R, C) is the sampling loop of edge e
+ * started with the t levels (R, C) already fixed.  Only nodes that meet the
+ * tile rows [row_tile_begin, row_tile_end) are split. */
+uint32_t orc_partition_word(uint64_t seed, int depth, uint64_t node, int j, uint64_t n);
+/* Binomial(n, p): inversion for n min(p, 1-p) < 10, else BTRS (Hoermann 1993);
+ * p > 1/2 draws n - Bin(n, 1 - p). */
+uint64_t orc_binomial(uint64_t n, double p, uint64_t seed, int depth, uint64_t node, int j);
+/* Non-empty tiles meeting the rows, at most `cap` written; returns how many
+ * there are (or -1 on invalid arguments). */
+int64_t orc_partition(double a, double b, double c, double d, int t, uint64_t m, uint64_t seed,
+                      uint64_t row_tile_begin, uint64_t row_tile_end, uint64_t cap,
+                      uint64_t *tile_row, uint64_t *tile_col, uint64_t *count, uint64_t *first);
+/* Edges first .. first+count-1 of tile (tile_row, tile_col) of a depth-t
+ * partition (single table). */
+int orc_generate_tile(const orc_table *table, int k, int t, uint64_t tile_row, uint64_t tile_col,
+                      uint64_t seed, uint64_t first, uint64_t count, uint64_t *row, uint64_t *col);
 
 /* Naive per-bit R-MAT (Sec. 1): level t draws one quadrant from word t with
  * thresholds round(a 2^32), round((a+b) 2^32), round((a+b+c) 2^32) of the

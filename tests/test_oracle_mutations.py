@@ -23,7 +23,8 @@ MUTATIONS = [
      [lambda: pins.test_table_sizes_fig1("variable", 12, 4093)]),
     ("Philox multiplier typo", "#define PHILOX_M0 0xD2511F53u", "#define PHILOX_M0 0xD2511F35u",
      [pins.test_philox_matches_independent_engine]),
-    ("Philox output words rotated", "return out[n % 4];", "return out[(n + 1) % 4];",
+    ("Philox output words rotated", "(uint32_t)e, (uint32_t)(e >> 32)};\n    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};\n    uint32_t out[4];\n    orc_philox4x32_10(ctr, key, out);\n    return out[n % 4];",
+     "(uint32_t)e, (uint32_t)(e >> 32)};\n    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};\n    uint32_t out[4];\n    orc_philox4x32_10(ctr, key, out);\n    return out[(n + 1) % 4];",
      [pins.test_philox_matches_independent_engine]),
     ("Vose drops a term", "rest[l] -= C - rest[s];", "rest[l] -= C;",
      [lambda: pins.test_weights_and_alias_roundtrip(lambda: oracle.Table.fixed([pins.ASYM], 4))]),
@@ -43,6 +44,19 @@ MUTATIONS = [
     ("scramble multiplier may be even", "out[2 * i] = (splitmix64_next(&st) | 1ull) & mask;",
      "out[2 * i] = splitmix64_next(&st) & mask;",
      [lambda: pins.test_scramble_is_a_bijection(12, 7), lambda: pins.test_scramble_is_a_bijection(16, 123456789)]),
+    ("split sends b's edges to c's quadrant", "    part_rec(x, depth + 1, 2 * R, 2 * C + 1, nb);      /* b: upper right */\n    part_rec(x, depth + 1, 2 * R + 1, 2 * C, nc);",
+     "    part_rec(x, depth + 1, 2 * R, 2 * C + 1, nc);      /* b: upper right */\n    part_rec(x, depth + 1, 2 * R + 1, 2 * C, nb);",
+     [pins.test_quadrant_split_is_multinomial]),
+    ("b conditioned on b + c only", "const double den_b = (P[1] + P[2]) + P[3]", "const double den_b = (P[1] + P[2])",
+     [pins.test_quadrant_split_is_multinomial]),
+    ("inversion recurrence off by one", "f *= a / (double)x - sr;", "f *= a / (double)(x + 1) - sr;",
+     [lambda: pins.test_binomial_matches_exact_pmf(7, 0.3), lambda: pins.test_binomial_matches_exact_pmf(40, 0.2)]),
+    ("BTRS candidate shifted", "const double c = nd * p + 0.5;", "const double c = nd * p + 1.5;",
+     [lambda: pins.test_binomial_matches_exact_pmf(60, 0.4), lambda: pins.test_binomial_matches_exact_pmf(100, 0.5)]),
+    ("tile prefix dropped", "        uint64_t r = pre_r, c = pre_c;", "        uint64_t r = pre_r, c = 0;",
+     [pins.test_partitioned_graph_has_the_kronecker_distribution]),
+    ("edge numbering restarts in every tile", "x->first[x->n] = x->next;", "x->first[x->n] = 0;",
+     [pins.test_tile_counts_expectation_and_numbering]),
 ]
 
 

@@ -454,3 +454,130 @@ def test_scramble_relabels_vertices_only():
     cc = np.concatenate([[counts[order][small].sum()], counts[order][~small]])
     pp = np.concatenate([[probs[order][small].sum()], probs[order][~small]])
     assert _chi2_pvalue(cc, pp) > 1e-3
+
+
+# ------------------------------------------------------ partitioned graphs --
+
+def _binned_gof(samples, n, p, min_expected=20.0):
+    """Chi-square p-value of integer samples against the exact Bin(n, p) pmf
+    (scipy), tails pooled until every bin expects >= min_expected."""
+    samples = np.asarray(samples, np.int64)
+    N = len(samples)
+    lo = int(stats.binom.ppf(1e-7, n, p))
+    hi = int(stats.binom.ppf(1 - 1e-7, n, p))
+    xs = np.arange(lo, hi + 1)
+    pmf = stats.binom.pmf(xs, n, p)
+    pmf[0] += stats.binom.cdf(lo - 1, n, p)
+    pmf[-1] += stats.binom.sf(hi, n, p)
+    cnt = np.bincount(np.clip(samples, lo, hi) - lo, minlength=len(xs)).astype(float)
+    # pool adjacent bins left to right until each expects enough
+    ec, pc, acc_c, acc_p = [], [], 0.0, 0.0
+    for c, q in zip(cnt, pmf):
+        acc_c += c
+        acc_p += q
+        if acc_p * N >= min_expected:
+            ec.append(acc_c)
+            pc.append(acc_p)
+            acc_c = acc_p = 0.0
+    if acc_p > 0:
+        ec[-1] += acc_c
+        pc[-1] += acc_p
+    return _chi2_pvalue(np.array(ec), np.array(pc))
+
+
+@pytest.mark.parametrize("n,p", [(7, 0.3), (40, 0.2), (2000, 0.004),      # inversion
+                                 (60, 0.4), (100, 0.5), (10 ** 6, 0.19),  # BTRS
+                                 (25, 0.85), (3000, 0.57)])               # n - Bin(n, 1 - p)
+def test_binomial_matches_exact_pmf(n, p):
+    xs = [oracle.binomial(n, p, 11, 7, node, 1) for node in range(20000)]
+    assert min(xs) >= 0 and max(xs) <= n
+    assert _binned_gof(xs, n, p) > 1e-3
+
+
+def test_binomial_degenerate_cases_and_large_n():
+    assert oracle.binomial(0, 0.3, 1, 0, 0, 0) == 0
+    assert oracle.binomial(12345, 0.0, 1, 0, 0, 0) == 0
+    assert oracle.binomial(12345, 1.0, 1, 0, 0, 0) == 12345
+    n, p = 1 << 30, 0.57
+    xs = np.array([oracle.binomial(n, p, 3, 1, node, 0) for node in range(3000)], np.float64)
+    sd = math.sqrt(n * p * (1 - p))
+    assert abs(xs.mean() - n * p) < 5 * sd / math.sqrt(len(xs))
+    assert 0.9 < xs.var() / sd ** 2 < 1.1
+
+
+def test_quadrant_split_is_multinomial():
+    """The three conditional binomials of one split give the multinomial law
+    of (n_a, n_b, n_c, n_d) with the quadrants in a, b, c, d order (b != c so
+    a swapped pair shows); m = 3: all 20 outcomes."""
+    m, S = 3, 30000
+    outcomes = [o for o in itertools.product(range(m + 1), repeat=4) if sum(o) == m]
+    index = {o: i for i, o in enumerate(outcomes)}
+    counts = np.zeros(len(outcomes))
+    for seed in range(S):
+        tl = oracle.partition(ASYM, 1, m, seed)
+        q = [0, 0, 0, 0]
+        for R, C, n in zip(tl["row"], tl["col"], tl["count"]):
+            q[2 * int(R) + int(C)] = int(n)
+        counts[index[tuple(q)]] += 1
+    probs = np.array([stats.multinomial.pmf(o, m, ASYM) for o in outcomes])
+    assert _chi2_pvalue(counts, probs) > 1e-3
+
+
+def test_tile_counts_expectation_and_numbering():
+    t, m, S = 2, 5000, 400
+    K = kronecker(ASYM, t)
+    tot = np.zeros((1 << t, 1 << t))
+    for seed in range(S):
+        tl = oracle.partition(ASYM, t, m, seed)
+        assert int(tl["count"].sum()) == m and (tl["count"] > 0).all()
+        assert np.array_equal(tl["first"], np.concatenate([[0], np.cumsum(tl["count"])[:-1]]).astype(np.uint64))
+        # quadtree order: interleaved bits (row, col) of the tiles increase
+        z = [sum(((int(r) >> b & 1) << (2 * b + 1)) | ((int(c) >> b & 1) << (2 * b)) for b in range(t))
+             for r, c in zip(tl["row"], tl["col"])]
+        assert z == sorted(z)
+        tot[tl["row"].astype(int), tl["col"].astype(int)] += tl["count"]
+    assert _chi2_pvalue(tot.ravel(), K.ravel()) > 1e-3
+
+
+def test_partition_rows_are_communication_free():
+    """A PE that owns some tile rows gets exactly the global tiles of those
+    rows, with the same counts and edge numbers."""
+    t, m = 5, 1 << 28
+    full = oracle.partition(G500, t, m, 9)
+    key = lambda d: {(int(r), int(c)): (int(n), int(f)) for r, c, n, f in zip(d["row"], d["col"], d["count"], d["first"])}
+    g = key(full)
+    seen = {}
+    for r0, r1 in [(0, 3), (3, 4), (4, 17), (17, 32)]:
+        part = key(oracle.partition(G500, t, m, 9, r0, r1))
+        assert all(r0 <= r < r1 for r, _ in part)
+        assert all(g[rc] == v for rc, v in part.items())
+        seen.update(part)
+    assert seen == g
+    assert sum(n for n, _ in g.values()) == m
+
+
+def test_partitioned_graph_has_the_kronecker_distribution():
+    k, t, m = 6, 2, 1 << 18
+    table = oracle.Table.variable(*ASYM, k, 40)
+    tiles, (r, c) = oracle.generate_partitioned(table, ASYM, k, t, m, 5)
+    assert len(r) == m
+    pos = 0
+    for R, C, n in zip(tiles["row"], tiles["col"], tiles["count"]):
+        sl = slice(pos, pos + int(n))
+        assert ((r[sl] >> np.uint64(k - t)) == R).all() and ((c[sl] >> np.uint64(k - t)) == C).all()
+        pos += int(n)
+    counts = np.bincount((r.astype(np.int64) << k) | c.astype(np.int64), minlength=1 << (2 * k)).astype(float)
+    probs = kronecker(ASYM, k).ravel()
+    order = np.argsort(probs)
+    small = np.cumsum(probs[order] * m) < 50
+    cc = np.concatenate([[counts[order][small].sum()], counts[order][~small]])
+    pp = np.concatenate([[probs[order][small].sum()], probs[order][~small]])
+    assert _chi2_pvalue(cc, pp) > 1e-3
+
+
+def test_partition_depth_zero_is_the_plain_graph():
+    table = oracle.Table.variable(*G500, 20, 500)
+    tiles, (r, c) = oracle.generate_partitioned(table, G500, 20, 0, 5000, 77)
+    assert list(tiles["count"]) == [5000] and list(tiles["first"]) == [0]
+    r0, c0 = oracle.generate([table], 20, 77, 0, 5000)
+    assert np.array_equal(r, r0) and np.array_equal(c, c0)

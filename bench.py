@@ -62,11 +62,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-edges", type=int, default=1 << 27)
-    ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5", "part"], default="c2",
                     help="c2 (default): the contract line; c1/c3/c4/c5: the other configurations, one JSON line each")
     ap.add_argument("--log2m", type=int, default=LOG2M,
                     help="c2: edges per GPU = 2^log2m (default 30; smaller only for profiling captures)")
     ap.add_argument("--graphs", type=int, default=4096, help="c4: number of graphs")
+    ap.add_argument("--tile-levels", type=int, default=5, help="part: tiles of 2^(k-t) x 2^(k-t) vertices")
     ap.add_argument("--wave-gib", type=float, default=48.0, help="c4: output budget per batched launch")
     ap.add_argument("--requests", type=int, default=256, help="c5: trace length")
     ap.add_argument("--rate", type=float, default=2000.0, help="c5: mean arrivals per second")
@@ -473,6 +474,35 @@ def run_c4(args):
                       "graphs_checked_bytewise": checked}), flush=True)
 
 
+def run_part(args):
+    """Partitioned k = 26, m = 2^30 graph (Sec. 3): host divide and conquer
+    for the tile counts, then every tile in one persistent batched launch;
+    the same graph size as the plain single launch beside it."""
+    import torch
+    import paper_1905_03525_gb300 as rm
+    k, m, t = K, 1 << args.log2m, args.tile_levels
+    table = rm.rmat_build_table(*G500, k, BOUND)
+    t0 = time.perf_counter()
+    p = rm.rmat_partition_create(table, t, m, SEED)
+    plan_s = time.perf_counter() - t0
+    ntiles, edges = rm.rmat_partition_info(p)
+    out = rm.empty_edges(edges, k)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(max(3, args.warmup)):
+            rm.rmat_generate_partition(p, out, s)
+        part_s = _events_time(lambda: rm.rmat_generate_partition(p, out, s), s, args.steps)
+        plain_s = _events_time(lambda: rm.rmat_generate(table, SEED, 0, m, out, s), s, args.steps)
+    rm.rmat_check_device_errors()
+    peak, peak_src = measured_peak()
+    print(json.dumps({"workload": "part", "config": {"workload": f"R-MAT k={k}, m=2^{args.log2m}, G500 parameters, "
+                      f"table bound {BOUND}, {1 << t}x{1 << t} tiles, one PE (all tile rows), u32", "tile_levels": t},
+                      "metric": "edges/s", "edges": edges, "tiles": ntiles, "host_plan_ms": plan_s * 1e3,
+                      "partitioned_edges_per_s": edges / part_s, "ms_per_launch": part_s * 1e3,
+                      "hbm_frac": 8.0 * edges / part_s / 1e9 / peak, "peak_source": peak_src,
+                      "plain_single_launch_edges_per_s": m / plain_s}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -483,6 +513,8 @@ def main():
         run_c3(args)
     elif args.workload == "c4":
         run_c4(args)
+    elif args.workload == "part":
+        run_part(args)
     elif args.workload == "c5":
         from paper_1905_03525_gb300 import serve
         serve.bench(args)

@@ -214,9 +214,23 @@ rmat_status rmat_batch_create(rmat_batch **out);
 rmat_status rmat_batch_add(rmat_batch *b, const rmat_table *t, uint64_t seed,
                            uint64_t edge_offset, uint64_t count, void *out);
 
+/* Add a tile of a partitioned graph (Sec. 3): edges edge_offset ..
+ * edge_offset+count-1, each started with its top tile_levels levels fixed to
+ * (tile_row, tile_col) -- the tile's rows [tile_row * 2^(k-tile_levels), ...)
+ * and columns likewise -- and the remaining k - tile_levels levels drawn from
+ * the edge's stream as in rmat_generate.  tile_levels = 0 is rmat_batch_add.
+ * The table must have one group (rmat_build_table or rmat_build_table_fixed)
+ * without RMAT_UNDIRECTED or scrambling (either would move edges out of the
+ * tile); tile_levels <= min(k, 30); coordinates < 2^tile_levels. */
+rmat_status rmat_batch_add_tile(rmat_batch *b, const rmat_table *t, uint64_t seed,
+                                uint64_t edge_offset, uint64_t count, int tile_levels,
+                                uint64_t tile_row, uint64_t tile_col, void *out);
+
 /* Pack table images and work list into device memory (synchronous; done
  * automatically by the first launch).  Call before graph capture.  cfg may be
- * NULL (default shape).
+ * NULL (default shape: 1024 threads, one CTA per SM, 512-edge tiles -- 256
+ * for k > 32 -- halved while the largest table would not fit in shared memory
+ * beside them).
  * Adding graphs after preparing discards the device state (and with it any
  * CUDA graph that captured rmat_batch_launch). */
 rmat_status rmat_batch_prepare(rmat_batch *b, const rmat_launch_config_t *cfg);
@@ -229,6 +243,55 @@ rmat_status rmat_batch_launch(rmat_batch *b, rmat_stream_t stream);
 rmat_status rmat_batch_size(const rmat_batch *b, uint64_t *graphs, uint64_t *edges);
 
 void rmat_batch_free(rmat_batch *b);
+
+/* ---------------------------------------------------------------------- */
+/* Partitioned graphs (Sec. 3: communication-free generation of partitioned */
+/* graphs, each PE holding all edges of some rows)                          */
+/* ---------------------------------------------------------------------- */
+/* The 2^k x 2^k adjacency matrix is cut into 2^t x 2^t square tiles
+ * (t = tile_levels).  Tile counts come from a divide-and-conquer pass over the
+ * quadtree: node (depth, R, C) holding n edges gives
+ *   n_a ~ Bin(n, a), n_b ~ Bin(n - n_a, b/(b+c+d)), n_c ~ Bin(n - n_a - n_b, c/(c+d)),
+ *   n_d = n - n_a - n_b - n_c
+ * to its children (2R, 2C), (2R, 2C+1), (2R+1, 2C), (2R+1, 2C+1), with (a, b,
+ * c, d) the table's normalised parameters.  Binomial j in {0, 1, 2} of node
+ * (depth, R, C) uses the Philox4x32-10 stream with key = seed and counter
+ * (n / 4, 2^31 | j << 8 | depth, node lo, node hi), node = R * 2^depth + C,
+ * word n % 4; a uniform is (x + 1/2) 2^-52 with x = (w0 >> 6) 2^26 + (w1 >> 6)
+ * of two consecutive words.  Bin(n, p) for p > 1/2 is n - Bin(n, 1 - p); for
+ * n p < 10 it is inversion by sequential search (restarting with a new
+ * uniform if the rounded pmf runs out), else BTRS (Hoermann 1993).
+ * Tiles are taken in quadtree order (a, b, c, d at every level) and the edges
+ * numbered consecutively in that order: a tile's edges are edge_offset =
+ * first .. first+count-1 of rmat_batch_add_tile.  A PE that owns tile rows
+ * [row_tile_begin, row_tile_end) splits only the nodes meeting them and gets
+ * exactly those tiles of the global partition (no communication). */
+typedef struct rmat_partition rmat_partition; /* opaque */
+
+/* Compute the tiles of this PE (host only, no device work).  The table (one
+ * group; not undirected, not scrambled) must outlive the partition.  Empty
+ * tiles are left out.  Errors: RMAT_ERR_INVALID_ARGUMENT (table kind,
+ * tile_levels outside [0, min(k, 30)], row range outside [0, 2^tile_levels]). */
+rmat_status rmat_partition_create(const rmat_table *t, int tile_levels, uint64_t m, uint64_t seed,
+                                  uint64_t row_tile_begin, uint64_t row_tile_end,
+                                  rmat_partition **out);
+
+/* Number of (non-empty) tiles of this PE and their total edges. */
+rmat_status rmat_partition_info(const rmat_partition *p, uint64_t *tiles, uint64_t *edges);
+
+/* Copy the tiles out, in quadtree order; each array (any may be NULL) holds
+ * `tiles` entries: tile row and column, edge count, first edge number. */
+rmat_status rmat_partition_tiles(const rmat_partition *p, uint64_t *tile_row, uint64_t *tile_col,
+                                 uint64_t *count, uint64_t *first_edge);
+
+/* Generate this PE's edges into `out` (device, 8-byte aligned, `edges`
+ * pairs of u32 for k <= 32, else u64), tile after tile in quadtree order, in
+ * one persistent batched launch (asynchronous on `stream`).  The first call
+ * for a given `out` prepares the launch (synchronous uploads); calls on one
+ * partition must not run concurrently, on the host or the device. */
+rmat_status rmat_generate_partition(rmat_partition *p, void *out, rmat_stream_t stream);
+
+void rmat_free_partition(rmat_partition *p);
 
 /* ---------------------------------------------------------------------- */
 /* Serving: continuous batching of generation requests                     */
@@ -329,7 +392,8 @@ void rmat_server_destroy(rmat_server *s);
  * that loads the library keeps until the process exits.
  *   - n <= RMAT_NOALLOC_MAX_GRAPHS; all tables of one call have the same
  *     output width (all k <= 32 or all k > 32); their blobs, the job list and
- *     one 4-byte entry per 32768 edges (16384 for k > 32) must fit the scratch.
+ *     one 4-byte entry per work unit (262144 edges; 131072 for k > 32 or
+ *     when a table is too large for the default tile) must fit the scratch.
  *     Anything larger returns RMAT_ERR_INVALID_ARGUMENT and launches nothing.
  *   - The first call on a device looks up the scratch's device address (once
  *     per device, with that device current); make that first call before any

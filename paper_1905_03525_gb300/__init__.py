@@ -21,7 +21,8 @@ __all__ = [
     "rmat_generate_naive", "rmat_set_launch_config", "rmat_get_launch_config",
     "rmat_check_device_errors", "rmat_version", "edge_bytes", "empty_edges", "Batch", "rmat_batch_create",
     "rmat_batch_add", "rmat_batch_prepare", "rmat_batch_launch", "rmat_batch_size", "rmat_batch_free",
-    "rmat_generate_batch_noalloc",
+    "rmat_generate_batch_noalloc", "rmat_batch_add_tile", "Partition", "rmat_partition_create",
+    "rmat_partition_info", "rmat_partition_tiles", "rmat_generate_partition", "rmat_free_partition",
 ]
 
 
@@ -221,6 +222,15 @@ def rmat_batch_add(b: Batch, t: Table, seed: int, edge_offset: int, count: int, 
     b._tables.append(t)
 
 
+def rmat_batch_add_tile(b: Batch, t: Table, seed: int, edge_offset: int, count: int, tile_levels: int,
+                        tile_row: int, tile_col: int, out) -> None:
+    """A tile of a partitioned graph: edges started with their top
+    tile_levels levels fixed to (tile_row, tile_col)."""
+    check(lib().rmat_batch_add_tile(b.handle, t.handle, seed, edge_offset, count, tile_levels, tile_row, tile_col,
+                                    _ptr(out)))
+    b._tables.append(t)
+
+
 def rmat_batch_prepare(b: Batch, threads=None, ctas_per_sm=None, tile_edges=None) -> None:
     if threads is None and ctas_per_sm is None and tile_edges is None:
         check(lib().rmat_batch_prepare(b.handle, None))
@@ -263,3 +273,62 @@ def rmat_check_device_errors() -> None:
 
 def rmat_version() -> str:
     return lib().rmat_version().decode()
+
+
+class Partition:
+    """Owning handle of an ``rmat_partition``; keeps its table alive."""
+
+    def __init__(self, handle, table):
+        self._h = handle
+        self._table = table
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("partition already freed")
+        return self._h
+
+    def free(self):
+        if self._h:
+            lib().rmat_free_partition(self._h)
+            self._h = None
+            self._table = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def rmat_partition_create(t: Table, tile_levels: int, m: int, seed: int, row_tile_begin: int = 0,
+                          row_tile_end=None) -> Partition:
+    """Tiles of a depth-tile_levels partition of graph (t, m, seed) that meet
+    the tile rows [row_tile_begin, row_tile_end) (Sec. 3 partitioned graphs)."""
+    if row_tile_end is None:
+        row_tile_end = 1 << tile_levels
+    h = ctypes.c_void_p()
+    check(lib().rmat_partition_create(t.handle, tile_levels, m, seed, row_tile_begin, row_tile_end, ctypes.byref(h)))
+    return Partition(h, t)
+
+
+def rmat_partition_info(p: Partition):
+    n, e = ctypes.c_uint64(), ctypes.c_uint64()
+    check(lib().rmat_partition_info(p.handle, ctypes.byref(n), ctypes.byref(e)))
+    return n.value, e.value
+
+
+def rmat_partition_tiles(p: Partition) -> dict:
+    n, _ = rmat_partition_info(p)
+    out = {f: np.zeros(max(n, 1), np.uint64) for f in ("row", "col", "count", "first")}
+    check(lib().rmat_partition_tiles(p.handle, _ptr(out["row"]), _ptr(out["col"]), _ptr(out["count"]),
+                                     _ptr(out["first"])))
+    return {f: a[:n] for f, a in out.items()}
+
+
+def rmat_generate_partition(p: Partition, out, stream=None) -> None:
+    check(lib().rmat_generate_partition(p.handle, _ptr(out), _stream(stream)))
+
+
+def rmat_free_partition(p: Partition) -> None:
+    p.free()

@@ -79,6 +79,12 @@ SIGNATURES = [
     ("rmat_build_table_levels", _st, [_vp, _i32, _i32, _u32, _vp]),
     ("rmat_table_set_flags", _st, [_vp, _u32]),
     ("rmat_table_set_scramble", _st, [_vp, _i32, _u64]),
+    ("rmat_batch_add_tile", _st, [_vp, _vp, _u64, _u64, _u64, _i32, _u64, _u64, _vp]),
+    ("rmat_partition_create", _st, [_vp, _i32, _u64, _u64, _u64, _u64, _vp]),
+    ("rmat_partition_info", _st, [_vp, _vp, _vp]),
+    ("rmat_partition_tiles", _st, [_vp, _vp, _vp, _vp, _vp]),
+    ("rmat_generate_partition", _st, [_vp, _vp, _vp]),
+    ("rmat_free_partition", None, [_vp]),
     ("rmat_table_info", _st, [_vp, _vp]),
     ("rmat_table_group_info", _st, [_vp, _i32, _vp, _vp, _vp]),
     ("rmat_table_export", _st, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),

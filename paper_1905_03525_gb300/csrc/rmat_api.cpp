@@ -164,6 +164,8 @@ rmat_status rmat_build_table(double a, double b, double c, double d, int k, uint
     rmat_table *t = new (std::nothrow) rmat_table;
     if (!t) return fail(RMAT_ERR_OUT_OF_MEMORY, "host allocation failed");
     t->k = k;
+    t->has_params = true;
+    std::copy(P, P + 4, t->params);
     t->groups.resize(1);
     try {
         if (rmat_status st = build_variable(P, k, table_bound, t->groups[0])) {
@@ -191,6 +193,8 @@ rmat_status rmat_build_table_fixed(double a, double b, double c, double d, int k
     rmat_table *t = new (std::nothrow) rmat_table;
     if (!t) return fail(RMAT_ERR_OUT_OF_MEMORY, "host allocation failed");
     t->k = k;
+    t->has_params = true;
+    std::copy(P, P + 4, t->params);
     t->groups.resize(1);
     try {
         if (rmat_status st = build_fixed(levels.data(), ell, t->groups[0])) {

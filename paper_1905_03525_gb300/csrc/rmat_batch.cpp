@@ -48,12 +48,15 @@ struct rmat_batch {
         const rmat_table *t;
         uint64_t seed, e0, count;
         void *out;
+        int tile_levels;  // > 0: a tile of a partitioned graph
+        uint64_t tile_row, tile_col;
     };
     std::vector<Entry> entries;
     bool prepared = false;
     int device = -1;
     Side side[2];
-    rmat_launch_config_t cfg{1024, 1, 256};
+    rmat_launch_config_t cfg{1024, 1, 512};
+    bool cfg_set = false;  // else the tile adapts to the tables (prepare_side)
     uint64_t edges = 0;
 };
 
@@ -83,6 +86,17 @@ rmat_status prepare_side(rmat_batch *b, bool u64, const DeviceProps &props, Side
 
     int threads = std::max(128, std::min(1024, b->cfg.threads / 32 * 32));
     int tile = std::max(32, std::min(1024, b->cfg.tile_edges / 32 * 32));
+    size_t largest_blob = 0;
+    for (const auto *en : mine) largest_blob = std::max(largest_blob, en->t->image.size() * 4);
+    if (!b->cfg_set) {
+        // Default shape: 512-edge tiles (256 for u64) fill phase 2's batches
+        // best; halve the tile while the largest table would not fit in
+        // shared memory beside the warps' tiles.
+        tile = u64 ? 256 : 512;
+        while (tile > (u64 ? 128 : 256) &&
+               16 + size_t(threads / 32) * warp_bytes(u64, false, tile) + largest_blob > size_t(props.max_smem))
+            tile /= 2;
+    }
     const size_t per_warp = warp_bytes(u64, false, tile);
     while (16 + size_t(threads / 32) * per_warp > size_t(props.max_smem) && threads > 128) threads /= 2;
     const size_t warps_bytes = size_t(threads / 32) * per_warp;
@@ -106,7 +120,9 @@ rmat_status prepare_side(rmat_batch *b, bool u64, const DeviceProps &props, Side
         if (e != cudaSuccess) return cuda_err("batch arena upload", e);
     }
 
-    const uint64_t unit_edges = uint64_t(threads / 32) * tile * 4;
+    // 16 tiles per warp per unit: the CTA waits for its slowest warp once per
+    // unit, and 2^30 edges still make ~27 units per CTA for the final wave.
+    const uint64_t unit_edges = uint64_t(threads / 32) * tile * 16;
     std::vector<Job> jobs;
     std::vector<Scramble> scrs;
     jobs.reserve(mine.size());
@@ -117,6 +133,7 @@ rmat_status prepare_side(rmat_batch *b, bool u64, const DeviceProps &props, Side
             reinterpret_cast<const uint32_t *>(static_cast<unsigned char *>(s.arena) + offset[en->t]);
         const bool smem = en->t->image.size() * 4 <= budget;
         Job J = make_job(en->t, blob, smem, en->seed, en->e0, en->count, en->out);
+        if (en->tile_levels) set_tile_prefix(J, en->t, en->tile_levels, en->tile_row, en->tile_col);
         J.unit_begin = units;
         units += (en->count + unit_edges - 1) / unit_edges;
         jobs.push_back(J);
@@ -157,6 +174,7 @@ rmat_status prepare_side(rmat_batch *b, bool u64, const DeviceProps &props, Side
     s.args.max_blob_bytes = max_blob;
     s.args.tile = tile;
     s.args.err = props.err;
+    for (const Job &J : jobs) s.args.prefixed |= J.pre_len ? 1 : 0;
     return RMAT_OK;
 }
 
@@ -184,12 +202,32 @@ rmat_status rmat_batch_add(rmat_batch *b, const rmat_table *t, uint64_t seed, ui
     if (count > ~uint64_t(0) - edge_offset)
         return fail(RMAT_ERR_INVALID_ARGUMENT, "edge_offset + count overflows 64 bits");
     if (b->entries.size() >= 0xFFFFFFFFu) return fail(RMAT_ERR_INVALID_ARGUMENT, "too many graphs");
-    b->entries.push_back({t, seed, edge_offset, count, out});
+    b->entries.push_back({t, seed, edge_offset, count, out, 0, 0, 0});
     b->edges += count;
     if (b->prepared) {
         for (Side &s : b->side) free_side(s);
         b->prepared = false;
     }
+    return RMAT_OK;
+}
+
+rmat_status rmat_batch_add_tile(rmat_batch *b, const rmat_table *t, uint64_t seed, uint64_t edge_offset,
+                                uint64_t count, int tile_levels, uint64_t tile_row, uint64_t tile_col, void *out) {
+    clear_error();
+    if (!b || !t) return fail(RMAT_ERR_INVALID_ARGUMENT, "NULL batch or table");
+    if (t->per_level || t->groups.size() != 1)
+        return fail(RMAT_ERR_INVALID_ARGUMENT, "tiles take a single-group (variable or fixed) table");
+    if (t->flags & RMAT_UNDIRECTED || t->scramble)
+        return fail(RMAT_ERR_INVALID_ARGUMENT, "a tile keeps its edges: no undirected mirroring, no scrambling");
+    if (tile_levels < 0 || tile_levels > t->k || tile_levels > 30)
+        return fail(RMAT_ERR_INVALID_ARGUMENT, "tile_levels must be in [0, min(k, 30)]");
+    if ((tile_row >> tile_levels) || (tile_col >> tile_levels))
+        return fail(RMAT_ERR_INVALID_ARGUMENT, "tile coordinates must be < 2^tile_levels");
+    if (rmat_status st = rmat_batch_add(b, t, seed, edge_offset, count, out)) return st;
+    auto &en = b->entries.back();
+    en.tile_levels = tile_levels;
+    en.tile_row = tile_row;
+    en.tile_col = tile_col;
     return RMAT_OK;
 }
 
@@ -201,6 +239,7 @@ rmat_status rmat_batch_prepare(rmat_batch *b, const rmat_launch_config_t *cfg) {
             cfg->ctas_per_sm > 8 || cfg->tile_edges < 32 || cfg->tile_edges > 1024 || cfg->tile_edges % 32)
             return fail(RMAT_ERR_INVALID_ARGUMENT, "bad batch launch config");
         b->cfg = *cfg;
+        b->cfg_set = true;
     }
     DeviceProps props;
     if (rmat_status st = device_props(props)) return st;

@@ -75,6 +75,8 @@ struct rmat_table {
     std::vector<rmat::GroupDesc> gdesc;
     std::mutex mu;
     std::map<int, rmat::DeviceCopy> dev;    // device ordinal -> copy
+    bool has_params = false;                // one (a, b, c, d) for every level
+    double params[4] = {0, 0, 0, 0};        // ... normalised (partition splits)
     bool scramble = false;                  // relabel vertex IDs
     uint64_t scr[6] = {0, 0, 0, 0, 0, 0};   // m0, a0, m1, a1, m2, a2
     bool cfg_set = false;

@@ -79,8 +79,8 @@ __device__ __forceinline__ dev::Group<SMEM> group0(const Job &J, uint32_t sblob)
 // Philox block q of edge e under the job's key.  KS: round keys read from the
 // job's precomputed schedule (kernel parameter), else derived in registers.
 template <bool KS>
-__device__ __forceinline__ uint4 edge_block(const Job &J, uint32_t q, uint64_t e) {
-    if constexpr (KS) return dev::philox_ks(q, 0u, uint32_t(e), uint32_t(e >> 32), J.ks);
+__device__ __forceinline__ uint4 edge_block(const Job &J, const uint32_t (&ks)[20], uint32_t q, uint64_t e) {
+    if constexpr (KS) return dev::philox_ks(q, 0u, uint32_t(e), uint32_t(e >> 32), ks);
     else return dev::philox(q, 0u, uint32_t(e), uint32_t(e >> 32), J.key0, J.key1);
 }
 
@@ -149,9 +149,10 @@ __device__ __forceinline__ void put_final(uint32_t stage, uint32_t idx, const ty
 // edges go to their output slot; unfinished ones leave their raw accumulators
 // in the same slot, their level count in p_fill, and a bit in the lane's mask
 // (bit i = edge i*32 + lane).
-template <int FMT, bool U64, bool SMEM, int EPI, bool FULL, bool KS>
-__device__ __forceinline__ uint32_t phase1(const Job &J, const Scramble &S, const dev::Group<SMEM> &G0,
-                                           uint64_t ebase, uint32_t n, uint32_t stage, uint32_t p_fill, int lane) {
+template <int FMT, bool U64, bool SMEM, int EPI, bool FULL, bool KS, bool PRE>
+__device__ __forceinline__ uint32_t phase1(const Job &J, const uint32_t (&ks)[20], const Scramble &S,
+                                           const dev::Group<SMEM> &G0, uint64_t ebase, uint32_t n, uint32_t stage,
+                                           uint32_t p_fill, int lane) {
     using Acc = typename AccT<U64>::type;
     const uint32_t uk = uint32_t(J.k);
     uint32_t pm = 0;
@@ -182,11 +183,18 @@ __device__ __forceinline__ uint32_t phase1(const Job &J, const Scramble &S, cons
     };
     for (uint32_t it = 0; it < iters; it += 2) {
         const uint32_t idx0 = it * 32 + lane;
-        const uint4 w0 = edge_block<KS>(J, 0u, ebase + idx0);
-        const uint4 w1 = edge_block<KS>(J, 0u, ebase + idx0 + 32);
+        const uint4 w0 = edge_block<KS>(J, ks, 0u, ebase + idx0);
+        const uint4 w1 = edge_block<KS>(J, ks, 0u, ebase + idx0 + 32);
         Acc a0, a1;
         a0.clear();
         a1.clear();
+        if constexpr (PRE) {
+            // batched jobs may start below the top level (a partition tile)
+            using Word = typename AccT<U64>::word;
+            a0.row = a1.row = Word(J.pre_row);
+            a0.col = a1.col = Word(J.pre_col);
+            a0.filled = a1.filled = J.pre_len;
+        }
         step(a0, w0.x);
         step(a1, w1.x);
         if (J.draws1 > 1) {
@@ -210,10 +218,13 @@ __device__ __forceinline__ uint32_t phase1(const Job &J, const Scramble &S, cons
 // sgroups: shared address of precomputed group descriptors (uint4 {A, Bs, Ba,
 // 2^b} per group) for per-level tables staged in shared memory, or 0 to read
 // them from the blob header at every draw.
-template <int FMT, bool U64, bool SMEM, bool LEVELS, int EPI, bool KS>
-__device__ __forceinline__ void gen_tile(const Job &J, const Scramble &S, uint32_t sblob, const uint32_t *gblob,
-                                         const dev::Group<SMEM> &G0, uint64_t first, uint32_t n, WarpState &W,
-                                         uint32_t sgroups = 0) {
+// KS: round keys from `ks` (a kernel parameter: constant-bank operands), else
+// derived from the job's key in registers.  PRE: edges start with the job's
+// prefix levels (batched jobs).
+template <int FMT, bool U64, bool SMEM, bool LEVELS, int EPI, bool KS, bool PRE>
+__device__ __forceinline__ void gen_tile(const Job &J, const uint32_t (&ks)[20], const Scramble &S, uint32_t sblob,
+                                         const uint32_t *gblob, const dev::Group<SMEM> &G0, uint64_t first,
+                                         uint32_t n, WarpState &W, uint32_t sgroups = 0) {
     using Acc = typename AccT<U64>::type;
     constexpr uint32_t EB = U64 ? 16 : 8;
     const int lane = W.lane;
@@ -234,7 +245,7 @@ __device__ __forceinline__ void gen_tile(const Job &J, const Scramble &S, uint32
             Acc acc;
             acc.clear();
             for (int q = 0; 4 * q < J.ngroups; ++q) {
-                const uint4 w = edge_block<KS>(J, uint32_t(q), e);
+                const uint4 w = edge_block<KS>(J, ks, uint32_t(q), e);
                 const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
@@ -258,8 +269,9 @@ __device__ __forceinline__ void gen_tile(const Job &J, const Scramble &S, uint32
         }
     } else {
         const uint32_t pm = n == uint32_t(W.tile)
-                                ? phase1<FMT, U64, SMEM, EPI, true, KS>(J, S, G0, ebase, n, stage, p_fill, lane)
-                                : phase1<FMT, U64, SMEM, EPI, false, KS>(J, S, G0, ebase, n, stage, p_fill, lane);
+                                ? phase1<FMT, U64, SMEM, EPI, true, KS, PRE>(J, ks, S, G0, ebase, n, stage, p_fill, lane)
+                                : phase1<FMT, U64, SMEM, EPI, false, KS, PRE>(J, ks, S, G0, ebase, n, stage, p_fill,
+                                                                              lane);
         // Phase 2: queue the unfinished edges of the whole tile (warp prefix
         // sum of the lanes' counts), then finish them 32 at a time.
         const uint32_t cnt = __popc(pm);
@@ -299,7 +311,7 @@ __device__ __forceinline__ void gen_tile(const Job &J, const Scramble &S, uint32
                 // another draw (a warp-uniform branch)
                 for (uint32_t q = 1; q <= 17; ++q) {
                     if (!__any_sync(0xffffffffu, acc.filled < uk)) break;
-                    const uint4 w = edge_block<KS>(J, q, e);
+                    const uint4 w = edge_block<KS>(J, ks, q, e);
                     if (U64) {
                         if (acc.filled < uk) dev::draw<FMT, SMEM>(G0, w.x, acc);
                     } else {
@@ -404,13 +416,13 @@ __global__ void __launch_bounds__(1024, 1) k_alias(const __grid_constant__ Job J
         const uint64_t first = t * tile;
         const uint64_t left = J.count - first;
         const uint32_t n = left < uint64_t(tile) ? uint32_t(left) : uint32_t(tile);
-        gen_tile<FMT, U64, SMEM, LEVELS, EPI, true>(J, S, sblob, J.blob, G0, first, n, W, sgroups);
+        gen_tile<FMT, U64, SMEM, LEVELS, EPI, true, false>(J, J.ks, S, sblob, J.blob, G0, first, n, W, sgroups);
     }
     if (lane == 0 && W.issued) dev::bulk_wait_all();
 }
 
 // One work unit of a batch: edges [u * unit_edges, ...) of job unit_job[u].
-template <bool U64, int FMT, bool SMEM, bool LEVELS, int EPI>
+template <bool U64, int FMT, bool SMEM, bool LEVELS, int EPI, bool PRE>
 __device__ __forceinline__ void batch_unit(const Job &J, const Scramble &S, uint32_t sblob, uint64_t local_unit,
                                            uint64_t unit_edges, int nwarps, int warp, WarpState &W) {
     const dev::Group<SMEM> G0 = group0<SMEM>(J, sblob);
@@ -419,11 +431,13 @@ __device__ __forceinline__ void batch_unit(const Job &J, const Scramble &S, uint
     for (uint64_t first = f0 + uint64_t(warp) * W.tile; first < end; first += uint64_t(nwarps) * W.tile) {
         const uint64_t left = end - first;
         const uint32_t n = left < uint64_t(W.tile) ? uint32_t(left) : uint32_t(W.tile);
-        gen_tile<FMT, U64, SMEM, LEVELS, EPI, false>(J, S, sblob, J.blob, G0, first, n, W);
+        gen_tile<FMT, U64, SMEM, LEVELS, EPI, false, PRE>(J, J.ks, S, sblob, J.blob, G0, first, n, W);
     }
 }
 
-template <bool U64>
+// PRE: some job starts below the top level (a partition tile); the variant
+// without it keeps the job's prefix out of the registers.
+template <bool U64, bool PRE>
 __global__ void __launch_bounds__(1024) k_batch(BatchArgs B) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
@@ -474,7 +488,8 @@ __global__ void __launch_bounds__(1024) k_batch(BatchArgs B) {
         const uint64_t local = unit - J.unit_begin;
         const int sel = (J.fmt ? 8 : 0) | (J.smem ? 4 : 0) | (J.levels ? 2 : 0) | ((J.flags & RMAT_UNDIRECTED) ? 1 : 0);
         const Scramble &S = B.scr[jid];  // read (from global memory) only when relabelling
-#define RMAT_UNIT(F, SM, L, U) batch_unit<U64, F, SM, L, (U ? kEpiUndir : 0) | kEpiScrFlag>(J, S, sblob, local, B.unit_edges, nwarps, warp, W)
+#define RMAT_UNIT(F, SM, L, U) \
+    batch_unit<U64, F, SM, L, (U ? kEpiUndir : 0) | kEpiScrFlag, PRE>(J, S, sblob, local, B.unit_edges, nwarps, warp, W)
         switch (sel) {
             case 0: RMAT_UNIT(0, false, false, false); break;
             case 1: RMAT_UNIT(0, false, false, true); break;
@@ -756,6 +771,15 @@ Job make_job(const rmat_table *t, const uint32_t *dblob, bool smem, uint64_t see
     return J;
 }
 
+void set_tile_prefix(Job &J, const rmat_table *t, int levels, uint64_t R, uint64_t C) {
+    const int W = t->k > 32 ? 64 : 32;
+    J.pre_len = uint32_t(levels);
+    J.pre_row = levels ? R << (W - levels) : 0;
+    J.pre_col = levels ? C << (W - levels) : 0;
+    const int min_len = std::max(1, t->groups[0].min_len);
+    J.draws1 = std::max(1, std::min(4, (t->k - levels + min_len - 1) / min_len));
+}
+
 Scramble make_scramble(const rmat_table *t) {
     Scramble S{};
     if (!t->scramble) return S;
@@ -797,17 +821,30 @@ size_t batch_smem_bytes(bool u64, int threads, int tile, uint32_t max_blob_bytes
     return 16 + size_t(max_blob_bytes) + size_t(threads / 32) * warp_region_bytes(u64, false, tile);
 }
 
+void *batch_kernel(bool u64, bool prefixed) {
+    if (u64) return prefixed ? reinterpret_cast<void *>(&k_batch<true, true>)
+                             : reinterpret_cast<void *>(&k_batch<true, false>);
+    return prefixed ? reinterpret_cast<void *>(&k_batch<false, true>) : reinterpret_cast<void *>(&k_batch<false, false>);
+}
+
 rmat_status batch_occupancy(bool u64, int threads, size_t smem, int &per_sm) {
-    void *fn = u64 ? reinterpret_cast<void *>(&k_batch<true>) : reinterpret_cast<void *>(&k_batch<false>);
-    cudaError_t e = set_smem_attr(fn, smem);
-    if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+    for (bool pre : {false, true}) {
+        const cudaError_t e = set_smem_attr(batch_kernel(u64, pre), smem);
+        if (e != cudaSuccess)
+            return fail(RMAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+    }
+    // the smaller occupancy of the two variants (same CTA shape)
+    int per_sm_pre = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel(u64, false), threads, smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_pre, batch_kernel(u64, true), threads, smem);
+    per_sm = std::min(per_sm, per_sm_pre);
     if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
     return RMAT_OK;
 }
 
 rmat_status launch_batch(bool u64, const BatchArgs &args, int grid, int threads, size_t smem, cudaStream_t stream) {
-    void *fn = u64 ? reinterpret_cast<void *>(&k_batch<true>) : reinterpret_cast<void *>(&k_batch<false>);
+    void *fn = batch_kernel(u64, args.prefixed != 0);
     cudaError_t e = cudaMemsetAsync(args.counter, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     BatchArgs a = args;

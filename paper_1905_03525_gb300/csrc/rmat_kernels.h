@@ -35,6 +35,10 @@ struct Job {
     uint32_t a0, bs0, ba0; // group 0: word offsets of A, Bs, Ba in the blob
     uint32_t bits0;        // group 0: b
     uint64_t unit_begin;   // first work unit of this job (batches)
+    // Batched jobs only: levels fixed before the first draw (the tile of a
+    // partitioned graph), left-aligned in the accumulator word.
+    uint64_t pre_row, pre_col;
+    uint32_t pre_len;
 };
 
 // Vertex relabelling constants of a job (used when flags & kScrambleFlag),
@@ -60,6 +64,7 @@ struct BatchArgs {
     uint32_t max_blob_bytes;   // shared bytes reserved for a staged blob
     int tile;
     unsigned *err;
+    int prefixed;              // some job is a partition tile (pre_len > 0)
 };
 
 rmat_status device_props(DeviceProps &out);
@@ -68,6 +73,9 @@ rmat_status plan_alias_launch(const rmat_table *t, const rmat_launch_config_t &w
 Job make_job(const rmat_table *t, const uint32_t *dblob, bool smem, uint64_t seed, uint64_t e0, uint64_t count,
              void *out);
 Scramble make_scramble(const rmat_table *t);
+// Start every edge of a batched job inside tile (R, C) of a depth-`levels`
+// partition: the tile's levels are fixed, the draws fill the other k - levels.
+void set_tile_prefix(Job &J, const rmat_table *t, int levels, uint64_t R, uint64_t C);
 rmat_status launch_alias(const rmat_table *t, const uint32_t *dblob, const AliasPlan &plan, uint64_t seed,
                          uint64_t e0, uint64_t count, void *out, cudaStream_t stream);
 size_t warp_bytes(bool u64, bool levels, int tile);

@@ -88,13 +88,20 @@ extern "C" rmat_status rmat_generate_batch_noalloc(const rmat_table *const *tabl
     unsigned char *scratch = nullptr;
     if (rmat_status st = scratch_address(dev, &scratch)) return st;
 
-    // Launch shape of the batched kernel (as rmat_batch_prepare's default).
+    // Launch shape of the batched kernel (as rmat_batch_prepare's default):
+    // 512-edge tiles (256 for u64), halved while the largest table would not
+    // fit in shared memory beside them.
     int threads = 1024;
-    const int tile = u64 ? 128 : 256;
+    size_t largest_blob = 0;
+    for (uint32_t i = 0; i < n; ++i) largest_blob = std::max(largest_blob, tables[i]->image.size() * 4);
+    int tile = u64 ? 256 : 512;
+    while (tile > (u64 ? 128 : 256) &&
+           16 + size_t(threads / 32) * warp_bytes(u64, false, tile) + largest_blob > size_t(props.max_smem))
+        tile /= 2;
     const size_t per_warp = warp_bytes(u64, false, tile);
     while (16 + size_t(threads / 32) * per_warp > size_t(props.max_smem) && threads > 128) threads /= 2;
     const size_t budget = size_t(props.max_smem) - 16 - size_t(threads / 32) * per_warp;
-    const uint64_t unit_edges = uint64_t(threads / 32) * tile * 4;
+    const uint64_t unit_edges = uint64_t(threads / 32) * tile * 16;  // as rmat_batch_prepare
 
     // Scratch layout: [counter][jobs][relabelling constants][unit -> job][table blobs].
     uint64_t units = 0;

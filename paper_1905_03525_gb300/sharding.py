@@ -20,3 +20,11 @@ def strong_range(rank: int, world: int, m: int) -> tuple[int, int]:
     base, extra = divmod(m, world)
     start = rank * base + min(rank, extra)
     return start, base + (1 if rank < extra else 0)
+
+
+def row_tiles(rank: int, world: int, tile_levels: int) -> tuple[int, int]:
+    """(row_tile_begin, row_tile_end) of `rank` for a partitioned graph
+    (Sec. 3): the 2^tile_levels tile rows split into `world` near-equal runs,
+    so rank r holds every edge whose row falls in its run and nothing is
+    exchanged."""
+    return strong_range(rank, world, 1 << tile_levels)[0], sum(strong_range(rank, world, 1 << tile_levels))

@@ -162,3 +162,47 @@ def test_server_create_fails_cleanly_without_a_device():
     from paper_1905_03525_gb300.serve import Server
     with pytest.raises(rm.RmatError):
         Server(1 << 30)
+
+
+@pytest.mark.parametrize("kind,params,k,t,m,seed,rows", [
+    ("variable", G500, 26, 5, 1 << 30, 1, None),
+    ("variable", SKEWED, 30, 8, 1 << 34, 7, (37, 200)),
+    ("fixed", ASYM, 16, 4, 1 << 20, 3, (5, 6)),
+    ("variable", G500, 20, 0, 12345, 9, None),
+    ("variable", ASYM, 12, 12, 3000, 2, (100, 4096)),
+    ("variable", G500, 40, 10, 1 << 40, 11, (0, 3)),
+    ("variable", (0.25, 0.25, 0.25, 0.25), 24, 6, 999_999, 5, None),
+    ("fixed", (1.0, 0.0, 0.0, 0.0), 10, 3, 777, 1, None),
+])
+def test_partition_tiles_match_oracle(kind, params, k, t, m, seed, rows):
+    """The library's host-side divide and conquer (its own Philox and
+    binomials) gives the oracle's tiles, counts and edge numbers exactly."""
+    table = rm.rmat_build_table(*params, k, 4096) if kind == "variable" else rm.rmat_build_table_fixed(*params, k, 4)
+    r0, r1 = rows if rows else (0, 1 << t)
+    p = rm.rmat_partition_create(table, t, m, seed, r0, r1)
+    got = rm.rmat_partition_tiles(p)
+    ref = oracle.partition(params, t, m, seed, r0, r1)
+    for f in ("row", "col", "count", "first"):
+        assert np.array_equal(got[f], ref[f]), f
+    assert rm.rmat_partition_info(p) == (len(ref["row"]), int(ref["count"].sum()))
+
+
+def test_partition_host_checks():
+    t = rm.rmat_build_table(*G500, 20, 1024)
+    for args in [(21, 100, 1, 0, 1 << 21), (5, 100, 1, 3, 2), (5, 100, 1, 0, 33), (-1, 100, 1, 0, 1)]:
+        with pytest.raises(rm.RmatError):
+            rm.rmat_partition_create(t, *args)
+    lv = rm.rmat_build_table_levels(noisy_levels(20), 20, 5)
+    with pytest.raises(rm.RmatError):
+        rm.rmat_partition_create(lv, 3, 100, 1)
+    u = rm.rmat_build_table(*G500, 20, 1024)
+    rm.rmat_table_set_flags(u, rm.RMAT_UNDIRECTED)
+    with pytest.raises(rm.RmatError):
+        rm.rmat_partition_create(u, 3, 100, 1)
+    b = rm.rmat_batch_create()
+    with pytest.raises(rm.RmatError):
+        rm.rmat_batch_add_tile(b, t, 1, 0, 10, 4, 16, 0, 8)    # tile row >= 2^4
+    with pytest.raises(rm.RmatError):
+        rm.rmat_batch_add_tile(b, lv, 1, 0, 10, 5, 0, 0, 8)    # per-level table
+    rm.rmat_batch_add_tile(b, t, 1, 0, 10, 4, 15, 3, 8)
+    assert rm.rmat_batch_size(b) == (1, 10)

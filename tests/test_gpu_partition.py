@@ -1,0 +1,124 @@
+"""GPU parity for partitioned graphs (Sec. 3): every PE's tiles generated by
+the batched kernel with the tile levels fixed, against the CPU oracle, bit for
+bit, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1905_03525_gb300 as rm
+from paper_1905_03525_gb300.workloads import G500, SKEWED
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ASYM = (0.5, 0.2, 0.25, 0.05)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1905_03525_gb300 import build
+    build.build()
+    yield
+    torch.cuda.synchronize()
+    rm.rmat_check_device_errors()
+
+
+def pairs(t, k):
+    h = t.cpu().numpy()
+    h = h.view(np.uint32) if k <= 32 else h.view(np.uint64)
+    return h[:, 0].astype(np.uint64), h[:, 1].astype(np.uint64)
+
+
+def assert_same(gpu, ref):
+    bad = np.nonzero((gpu[0] != ref[0]) | (gpu[1] != ref[1]))[0]
+    assert bad.size == 0, f"{bad.size} edges differ; first at {bad[:5]}"
+
+
+@pytest.mark.parametrize("kind,params,k,t,m,seed,rows", [
+    ("variable", G500, 20, 3, 300_001, 1, None),           # several tiles, ragged counts
+    ("variable", ASYM, 12, 0, 70_000, 2, None),            # one tile = the plain graph
+    ("fixed", ASYM, 16, 4, 200_000, 3, (5, 9)),            # one PE's rows
+    ("variable", SKEWED, 30, 6, 150_000, 4, (0, 7)),       # wide path entries
+    ("variable", G500, 40, 5, 60_000, 5, None),            # u64 output
+    ("variable", G500, 14, 14, 5_000, 6, None),            # tiles of one cell: no draws
+    ("variable", G500, 26, 2, 1, 7, None),                 # a single edge
+])
+def test_partition_matches_oracle(kind, params, k, t, m, seed, rows):
+    table = rm.rmat_build_table(*params, k, 4096) if kind == "variable" else rm.rmat_build_table_fixed(*params, k, 4)
+    ot = oracle.Table.variable(*params, k, 4096) if kind == "variable" else oracle.Table.fixed([params], 4)
+    r0, r1 = rows if rows else (0, 1 << t)
+    p = rm.rmat_partition_create(table, t, m, seed, r0, r1)
+    ntiles, edges = rm.rmat_partition_info(p)
+    out = rm.empty_edges(max(edges, 1), k)
+    rm.rmat_generate_partition(p, out)
+    torch.cuda.synchronize()
+    tiles, ref = oracle.generate_partitioned(ot, params, k, t, m, seed, r0, r1)
+    assert ntiles == len(tiles["row"]) and edges == len(ref[0])
+    assert_same(pairs(out[:edges], k), ref)
+    if t == 0:
+        plain = rm.empty_edges(m, k)
+        rm.rmat_generate(table, seed, 0, m, plain)
+        torch.cuda.synchronize()
+        assert torch.equal(plain, out[:m])
+
+
+def test_batch_tiles_mix_with_plain_graphs():
+    """Tiles of two partitions and plain graphs in one batched launch."""
+    ta = rm.rmat_build_table(*G500, 22, 2048)
+    tb = rm.rmat_build_table_fixed(*ASYM, 18, 5)
+    oa, ob = oracle.Table.variable(*G500, 22, 2048), oracle.Table.fixed([ASYM], 5)
+    b = rm.rmat_batch_create()
+    cases = [(ta, oa, 22, 4, 11, 5, 9, 40_000, 3), (tb, ob, 18, 7, 100, 27, 1, 33_333, 0),
+             (ta, oa, 22, 0, 0, 0, 4, 25_000, 77)]
+    outs = []
+    for t, _, k, lv, R, C, seed, n, first in cases:
+        o = rm.empty_edges(n, k)
+        rm.rmat_batch_add_tile(b, t, seed, first, n, lv, R, C, o)
+        outs.append(o)
+    rm.rmat_batch_launch(b)
+    torch.cuda.synchronize()
+    for (t, ot, k, lv, R, C, seed, n, first), o in zip(cases, outs):
+        assert_same(pairs(o, k), oracle.generate_tile(ot, k, lv, R, C, seed, first, n))
+
+
+def test_partition_output_buffer_can_change():
+    table = rm.rmat_build_table(*G500, 20, 4096)
+    p = rm.rmat_partition_create(table, 4, 100_000, 8)
+    _, edges = rm.rmat_partition_info(p)
+    a, b = rm.empty_edges(edges, 20), rm.empty_edges(edges + 1, 20)
+    rm.rmat_generate_partition(p, a)
+    rm.rmat_generate_partition(p, b[1:])     # another (8-byte aligned) buffer
+    rm.rmat_generate_partition(p, a)         # and back
+    torch.cuda.synchronize()
+    assert torch.equal(a, b[1:])
+
+
+def test_partition_full_size_two_pes():
+    """k = 26, m = 2^30 in 2^5 x 2^5 tiles, split over two PEs by tile rows:
+    together they hold every edge once; sampled tiles match the oracle and
+    every edge lies in its tile."""
+    k, t, m, seed = 26, 5, 1 << 30, 1
+    table = rm.rmat_build_table(*G500, k, 4096)
+    ot = oracle.Table.variable(*G500, k, 4096)
+    total = 0
+    rng = np.random.default_rng(5)
+    for r0, r1 in [(0, 9), (9, 32)]:
+        p = rm.rmat_partition_create(table, t, m, seed, r0, r1)
+        tl = rm.rmat_partition_tiles(p)
+        ntiles, edges = rm.rmat_partition_info(p)
+        total += edges
+        out = rm.empty_edges(edges, k)
+        rm.rmat_generate_partition(p, out)
+        torch.cuda.synchronize()
+        rows = out[:, 0].view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+        assert int((rows >> (k - t)).min()) >= r0 and int((rows >> (k - t)).max()) < r1
+        pos = np.concatenate([[0], np.cumsum(tl["count"])]).astype(np.int64)
+        for i in rng.choice(ntiles, 12, replace=False):
+            n = int(min(tl["count"][i], 1500))
+            s = int(pos[i]) + int(tl["count"][i]) - n           # the tile's last n edges
+            ref = oracle.generate_tile(ot, k, t, int(tl["row"][i]), int(tl["col"][i]), seed,
+                                       int(tl["first"][i]) + int(tl["count"][i]) - n, n)
+            assert_same(pairs(out[s:s + n], k), ref)
+        del out
+        torch.cuda.empty_cache()
+    assert total == m

@@ -73,3 +73,64 @@ def test_strong_ranges_cover_exactly():
             spans = [strong_range(r, world, m) for r in range(world)]
             assert sum(c for _, c in spans) == m
             assert all(spans[i][0] + spans[i][1] == spans[i + 1][0] for i in range(world - 1))
+
+
+def _partition_rank(rank, world, port, q):
+    import oracle
+    import paper_1905_03525_gb300 as rm
+    from paper_1905_03525_gb300.sharding import row_tiles
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    k, t, m, seed = 14, 3, 40_000, 21
+    r0, r1 = row_tiles(rank, world, t)
+    # tiles from the library's host code (no device needed), edges from the oracle
+    table = rm.rmat_build_table(0.57, 0.19, 0.19, 0.05, k, 1024)
+    tiles = rm.rmat_partition_tiles(rm.rmat_partition_create(table, t, m, seed, r0, r1))
+    ot = oracle.Table.variable(0.57, 0.19, 0.19, 0.05, k, 1024)
+    _, (r, c) = oracle.generate_partitioned(ot, (0.57, 0.19, 0.19, 0.05), k, t, m, seed, r0, r1)
+    ok = bool(((r >> np.uint64(k - t)) >= r0).all() and ((r >> np.uint64(k - t)) < r1).all())
+    parts = [None] * world
+    dist.all_gather_object(parts, (rank, tiles, r, c, ok))
+    if rank == 0:
+        q.put(parts)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_partition_rows_without_exchange():
+    """Partitioned graph (Sec. 3) over two ranks by tile rows: each rank's
+    tiles (library host code) and edges (oracle) hold only its rows, and
+    together they are exactly the one-rank partitioned graph."""
+    import oracle
+    from paper_1905_03525_gb300 import build
+    build.build()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_partition_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    parts = q.get(timeout=180)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    parts.sort(key=lambda x: x[0])
+    assert all(p[4] for p in parts)
+    ot = oracle.Table.variable(0.57, 0.19, 0.19, 0.05, 14, 1024)
+    full, (r, c) = oracle.generate_partitioned(ot, (0.57, 0.19, 0.19, 0.05), 14, 3, 40_000, 21)
+    got = {}
+    for _, tiles, _, _, _ in parts:
+        for R, C, n, f in zip(tiles["row"], tiles["col"], tiles["count"], tiles["first"]):
+            got[int(f)] = (int(R), int(C), int(n))
+    want = {int(f): (int(R), int(C), int(n)) for R, C, n, f in zip(full["row"], full["col"], full["count"], full["first"])}
+    assert got == want
+    # edges: every global edge once, identified by its number within the graph
+    by_first = {}
+    for _, tiles, rr, cc, _ in parts:
+        pos = 0
+        for n, f in zip(tiles["count"], tiles["first"]):
+            by_first[int(f)] = (rr[pos:pos + int(n)], cc[pos:pos + int(n)])
+            pos += int(n)
+    rows = np.concatenate([by_first[f][0] for f in sorted(by_first)])
+    cols = np.concatenate([by_first[f][1] for f in sorted(by_first)])
+    assert np.array_equal(rows, r) and np.array_equal(cols, c)

@@ -89,6 +89,21 @@ def _declare(L):
     L.orc_scramble.restype = u64
     L.orc_generate_scrambled.argtypes = [vp, i32, i32, i32, vp, u64, u64, u64, vp, vp]
     L.orc_generate_scrambled.restype = i32
+    L.orc_kron_table_variable.argtypes = [vp, i32, i32, u64]
+    L.orc_kron_table_variable.restype = vp
+    L.orc_kron_table_fixed.argtypes = [vp, i32, i32]
+    L.orc_kron_table_fixed.restype = vp
+    L.orc_kron_table_free.argtypes = [vp]
+    for name in ("orc_kron_table_entries", "orc_kron_table_bits", "orc_kron_table_max_len"):
+        getattr(L, name).argtypes = [vp]
+        getattr(L, name).restype = i32
+    L.orc_kron_table_get.argtypes = [vp] * 7
+    L.orc_kron_draw.argtypes = [vp, u32]
+    L.orc_kron_draw.restype = u32
+    L.orc_kron_generate.argtypes = [vp, i32, u64, u64, u64, vp, vp]
+    L.orc_kron_generate.restype = i32
+    L.orc_kron_edge_distribution.argtypes = [vp, i32, i32, vp]
+    L.orc_kron_edge_distribution.restype = i32
     L.orc_partition_word.argtypes = [u64, i32, u64, i32, u64]
     L.orc_partition_word.restype = u32
     L.orc_binomial.argtypes = [u64, dbl, u64, i32, u64, i32]
@@ -200,6 +215,66 @@ def generate_scrambled(tables, k, scramble_seed, seed, e0, count, undirected=Fal
     if rc != 0:
         raise ValueError("oracle rejected the generate arguments")
     return row, col
+
+
+class KronTable:
+    """Oracle table of a stochastic Kronecker graph with an n0 x n0 initiator."""
+
+    def __init__(self, handle, n0):
+        if not handle:
+            raise ValueError("oracle rejected the Kronecker table arguments")
+        self._h = ctypes.c_void_p(handle)
+        self.n0 = n0
+        L = lib()
+        self.entries = L.orc_kron_table_entries(self._h)
+        self.bits = L.orc_kron_table_bits(self._h)
+        self.max_len = L.orc_kron_table_max_len(self._h)
+        N = 1 << self.bits
+        self.sym = np.zeros((N, max(self.max_len, 1)), np.uint8)
+        self.len = np.zeros(N, np.uint8)
+        self.p = np.zeros(N, np.float64)
+        self.w = np.zeros(N, np.uint64)
+        self.thr = np.zeros(N, np.uint32)
+        self.alias = np.zeros(N, np.uint32)
+        L.orc_kron_table_get(self._h, _ptr(self.sym), _ptr(self.len), _ptr(self.p), _ptr(self.w),
+                             _ptr(self.thr), _ptr(self.alias))
+
+    @classmethod
+    def variable(cls, theta, n0, k, bound):
+        th = np.ascontiguousarray(theta, dtype=np.float64).reshape(n0 * n0)
+        return cls(lib().orc_kron_table_variable(_ptr(th), n0, k, bound), n0)
+
+    @classmethod
+    def fixed(cls, theta, n0, ell):
+        th = np.ascontiguousarray(theta, dtype=np.float64).reshape(n0 * n0)
+        return cls(lib().orc_kron_table_fixed(_ptr(th), n0, ell), n0)
+
+    def draw(self, u: int) -> int:
+        return int(lib().orc_kron_draw(self._h, u))
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None):
+                lib().orc_kron_table_free(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+
+def kron_generate(table, k, seed, e0, count):
+    row = np.zeros(count, np.uint64)
+    col = np.zeros(count, np.uint64)
+    if lib().orc_kron_generate(table._h, k, seed, e0, count, _ptr(row), _ptr(col)) != 0:
+        raise ValueError("oracle rejected the Kronecker generate arguments")
+    return row, col
+
+
+def kron_edge_distribution(table, k, quantised=False) -> np.ndarray:
+    nv = table.n0 ** k
+    out = np.zeros(nv * nv, np.float64)
+    if lib().orc_kron_edge_distribution(table._h, k, int(quantised), _ptr(out)) != 0:
+        raise ValueError("oracle rejected the distribution arguments")
+    return out.reshape(nv, nv)
 
 
 def partition_word(seed, depth, node, j, n) -> int:

@@ -453,6 +453,281 @@ int orc_generate(const orc_table *const *tables, int ngroups, int k, int undirec
 }
 
 /* ------------------------------------------------------------------ */
+/* Stochastic Kronecker graphs with an n0 x n0 initiator (Sec. 3: a    */
+/* larger matrix instead of the 2 x 2 one in the recursion).  Symbol   */
+/* s = n0 * i + j selects initiator cell (i, j), i.e. row digit i and  */
+/* column digit j of the level; a path is a sequence of symbols.       */
+/* ------------------------------------------------------------------ */
+#define KRON_MAX_DEPTH 40
+
+struct orc_ktable {
+    int n0, cap;
+    orc_table *base;   /* len, p, w, thr, alias, entries, bits, max_len */
+    uint8_t *sym;      /* N x KRON_MAX_DEPTH symbols, first level first */
+};
+
+typedef struct { double p; int len; uint8_t sym[KRON_MAX_DEPTH]; } kentry;
+
+/* Larger p first; equal p: lexicographically smaller symbol sequence first
+ * (readings R2 and R16). */
+static int k_before(const kentry *x, const kentry *y)
+{
+    if (x->p != y->p) return x->p > y->p;
+    int n = x->len < y->len ? x->len : y->len;
+    for (int i = 0; i < n; ++i)
+        if (x->sym[i] != y->sym[i]) return x->sym[i] < y->sym[i];
+    return x->len < y->len;
+}
+
+static int cmp_ksym(const void *a, const void *b)
+{
+    const kentry *x = (const kentry *)a, *y = (const kentry *)b;
+    int n = x->len < y->len ? x->len : y->len;
+    for (int i = 0; i < n; ++i)
+        if (x->sym[i] != y->sym[i]) return x->sym[i] < y->sym[i] ? -1 : 1;
+    return (x->len > y->len) - (x->len < y->len);
+}
+
+/* Plain array heap on k_before (sift up / sift down). */
+typedef struct { kentry *v; size_t n, cap; } kheap;
+
+static int kheap_push(kheap *h, const kentry *e)
+{
+    if (h->n == h->cap) {
+        size_t nc = h->cap ? 2 * h->cap : 64;
+        kentry *nv = (kentry *)realloc(h->v, nc * sizeof(kentry));
+        if (!nv) return -1;
+        h->v = nv; h->cap = nc;
+    }
+    size_t i = h->n++;
+    h->v[i] = *e;
+    while (i > 0) {
+        size_t parent = (i - 1) / 2;
+        if (!k_before(&h->v[i], &h->v[parent])) break;
+        kentry tmp = h->v[i]; h->v[i] = h->v[parent]; h->v[parent] = tmp;
+        i = parent;
+    }
+    return 0;
+}
+
+static kentry kheap_pop(kheap *h)
+{
+    kentry top = h->v[0];
+    h->v[0] = h->v[--h->n];
+    size_t i = 0;
+    for (;;) {
+        size_t l = 2 * i + 1, r = l + 1, best = i;
+        if (l < h->n && k_before(&h->v[l], &h->v[best])) best = l;
+        if (r < h->n && k_before(&h->v[r], &h->v[best])) best = r;
+        if (best == i) break;
+        kentry tmp = h->v[i]; h->v[i] = h->v[best]; h->v[best] = tmp;
+        i = best;
+    }
+    return top;
+}
+
+/* Depth cap: the longest path whose row (or column) digits stay below 2^32,
+ * i.e. the largest L with n0^L <= 2^32 (32 for n0 = 2), and at most k. */
+static int kron_cap(int n0, int k)
+{
+    int L = 0;
+    double v = 1.0;
+    while (v * n0 <= 4294967296.0) { v *= n0; ++L; }
+    return k < L ? k : L;
+}
+
+static int kron_normalise(const double *theta, int n0, double *out)
+{
+    int S = n0 * n0;
+    double s = 0.0;
+    for (int i = 0; i < S; ++i) {
+        if (!(theta[i] >= 0.0) || !isfinite(theta[i])) return -1;
+        s = s + theta[i];
+    }
+    if (!(fabs(s - 1.0) <= 1e-9)) return -1;
+    for (int i = 0; i < S; ++i) out[i] = theta[i] / s;
+    return 0;
+}
+
+/* Largest k with n0^k <= 2^64. */
+static int kron_max_k(int n0)
+{
+    int k = 0;
+    double v = 1.0;
+    while (v * n0 <= 18446744073709551616.0) { v *= n0; ++k; }
+    return k;
+}
+
+static orc_ktable *ktable_from(kentry *all, int entries, int n0, int cap)
+{
+    orc_ktable *t = (orc_ktable *)calloc(1, sizeof(orc_ktable));
+    if (!t) return NULL;
+    t->n0 = n0;
+    t->cap = cap;
+    t->base = table_alloc(entries);
+    if (!t->base) { free(t); return NULL; }
+    size_t N = (size_t)1 << t->base->bits;
+    t->sym = (uint8_t *)calloc(N * KRON_MAX_DEPTH, 1);
+    if (!t->sym) { orc_table_free(t->base); free(t); return NULL; }
+    for (int i = 0; i < entries; ++i) {
+        t->base->len[i] = (uint8_t)all[i].len;
+        t->base->p[i] = all[i].p;
+        memcpy(t->sym + (size_t)i * KRON_MAX_DEPTH, all[i].sym, (size_t)all[i].len);
+        if (all[i].len > t->base->max_len) t->base->max_len = all[i].len;
+    }
+    if (quantise_and_alias(t->base) != 0) { orc_kron_table_free(t); return NULL; }
+    return t;
+}
+
+orc_ktable *orc_kron_table_variable(const double *theta, int n0, int k, uint64_t bound)
+{
+    if (n0 < 2 || n0 > 16) return NULL;
+    const int S = n0 * n0;
+    if (k < 1 || k > kron_max_k(n0) || bound < (uint64_t)S + 1 || bound > ((uint64_t)1 << 24)) return NULL;
+    double P[256];
+    if (kron_normalise(theta, n0, P) != 0) return NULL;
+    const int cap = kron_cap(n0, k);
+
+    kheap heap = {0};
+    kentry *done = (kentry *)malloc((size_t)bound * sizeof(kentry));
+    if (!done) return NULL;
+    size_t ndone = 0;
+    kentry root;
+    memset(&root, 0, sizeof root);
+    root.p = 1.0;
+    if (kheap_push(&heap, &root) != 0) { free(done); return NULL; }
+    /* Reading R16: expand while |Q| + n0^2 - 1 < bound (R1 for n0 = 2). */
+    while (heap.n > 0 && heap.n + ndone + (size_t)(S - 1) < bound) {
+        kentry e = kheap_pop(&heap);
+        for (int s = 0; s < S; ++s) {
+            kentry child = e;
+            child.p = e.p * P[s];
+            child.sym[e.len] = (uint8_t)s;
+            child.len = e.len + 1;
+            if (child.len >= cap) done[ndone++] = child;
+            else if (kheap_push(&heap, &child) != 0) { free(heap.v); free(done); return NULL; }
+        }
+    }
+    int entries = (int)(heap.n + ndone);
+    kentry *all = (kentry *)malloc((size_t)entries * sizeof(kentry));
+    if (!all) { free(heap.v); free(done); return NULL; }
+    memcpy(all, done, ndone * sizeof(kentry));
+    memcpy(all + ndone, heap.v, heap.n * sizeof(kentry));
+    free(heap.v); free(done);
+    qsort(all, (size_t)entries, sizeof(kentry), cmp_ksym);   /* reading R4 */
+    orc_ktable *t = ktable_from(all, entries, n0, cap);
+    free(all);
+    return t;
+}
+
+orc_ktable *orc_kron_table_fixed(const double *theta, int n0, int ell)
+{
+    if (n0 < 2 || n0 > 16 || ell < 1) return NULL;
+    const int S = n0 * n0;
+    double entries_d = 1.0;
+    for (int i = 0; i < ell; ++i) entries_d *= S;
+    if (entries_d > (double)(1 << 24) || ell > kron_cap(n0, 64)) return NULL;
+    double P[256];
+    if (kron_normalise(theta, n0, P) != 0) return NULL;
+    int entries = (int)entries_d;
+    kentry *all = (kentry *)calloc((size_t)entries, sizeof(kentry));
+    if (!all) return NULL;
+    /* Entry i: symbols = the base-n0^2 digits of i, most significant first. */
+    for (int i = 0; i < entries; ++i) {
+        int x = i;
+        for (int lvl = ell - 1; lvl >= 0; --lvl) { all[i].sym[lvl] = (uint8_t)(x % S); x /= S; }
+        double p = 1.0;
+        for (int lvl = 0; lvl < ell; ++lvl) p = p * P[all[i].sym[lvl]];
+        all[i].p = p;
+        all[i].len = ell;
+    }
+    orc_ktable *t = ktable_from(all, entries, n0, ell);
+    free(all);
+    return t;
+}
+
+void orc_kron_table_free(orc_ktable *t)
+{
+    if (!t) return;
+    orc_table_free(t->base);
+    free(t->sym);
+    free(t);
+}
+
+int orc_kron_table_entries(const orc_ktable *t) { return t->base->entries; }
+int orc_kron_table_bits(const orc_ktable *t) { return t->base->bits; }
+int orc_kron_table_max_len(const orc_ktable *t) { return t->base->max_len; }
+
+void orc_kron_table_get(const orc_ktable *t, uint8_t *sym, uint8_t *len, double *p,
+                        uint64_t *w, uint32_t *thr, uint32_t *alias)
+{
+    size_t N = (size_t)1 << t->base->bits;
+    int L = t->base->max_len;
+    for (size_t i = 0; i < N; ++i)
+        if (sym) memcpy(sym + i * (size_t)L, t->sym + i * KRON_MAX_DEPTH, (size_t)L);
+    orc_table_get(t->base, NULL, len, p, w, thr, alias);
+}
+
+uint32_t orc_kron_draw(const orc_ktable *t, uint32_t u) { return orc_draw(t->base, u); }
+
+int orc_kron_generate(const orc_ktable *t, int k, uint64_t seed, uint64_t e0, uint64_t count,
+                      uint64_t *row, uint64_t *col)
+{
+    if (!t || k < 1 || k > kron_max_k(t->n0)) return -1;
+    const uint64_t n0 = (uint64_t)t->n0;
+    for (uint64_t i = 0; i < count; ++i) {
+        uint64_t e = e0 + i, r = 0, c = 0, n = 0;
+        int filled = 0;
+        while (filled < k) {
+            uint32_t sel = orc_draw(t->base, orc_word(seed, e, n));
+            n++;
+            int L = t->base->len[sel];
+            int take = L < k - filled ? L : k - filled;
+            for (int lvl = 0; lvl < take; ++lvl) {
+                int s = t->sym[(size_t)sel * KRON_MAX_DEPTH + lvl];
+                r = r * n0 + (uint64_t)(s / t->n0);
+                c = c * n0 + (uint64_t)(s % t->n0);
+            }
+            filled += take;
+        }
+        row[i] = r;
+        col[i] = c;
+    }
+    return 0;
+}
+
+static void kdist_rec(const orc_ktable *t, int k, int quantised, int filled, uint64_t r, uint64_t c,
+                      double prob, uint64_t nv, double *out)
+{
+    if (filled >= k) { out[r * nv + c] += prob; return; }
+    int N = 1 << t->base->bits;
+    for (int j = 0; j < N; ++j) {
+        double pj = quantised ? ldexp((double)t->base->w[j], -32) : t->base->p[j];
+        if (pj == 0.0) continue;
+        int L = t->base->len[j];
+        int take = L < k - filled ? L : k - filled;
+        uint64_t rr = r, cc = c;
+        for (int lvl = 0; lvl < take; ++lvl) {
+            int s = t->sym[(size_t)j * KRON_MAX_DEPTH + lvl];
+            rr = rr * (uint64_t)t->n0 + (uint64_t)(s / t->n0);
+            cc = cc * (uint64_t)t->n0 + (uint64_t)(s % t->n0);
+        }
+        kdist_rec(t, k, quantised, filled + take, rr, cc, prob * pj, nv, out);
+    }
+}
+
+int orc_kron_edge_distribution(const orc_ktable *t, int k, int quantised, double *out)
+{
+    if (!t || k < 1) return -1;
+    uint64_t nv = 1;
+    for (int i = 0; i < k; ++i) nv *= (uint64_t)t->n0;
+    if (nv > 4096) return -1;
+    memset(out, 0, (size_t)(nv * nv) * sizeof(double));
+    kdist_rec(t, k, quantised, 0, 0, 0, 1.0, nv, out);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* Partitioned graphs (Sec. 3, communication-free generation of       */
 /* partitioned graphs): a divide-and-conquer pass gives the number of */
 /* edges in each of the 2^t x 2^t tiles of the adjacency matrix, then */

@@ -18,6 +18,7 @@
  *   - the naive per-bit R-MAT process (k quadrant draws per edge)   [Sec. 1]
  *   - exact edge distribution implied by a table, by enumeration    [Sec. 1 definition, for pins]
  *   - scrambling: seeded bijective relabelling of vertex IDs        [Sec. 3]
+ *   - Kronecker initiators of size n0 x n0 (tables, generation)     [Sec. 3]
  *   - partitioned graphs: divide-and-conquer tile edge counts by    [Sec. 3]
  *     binomial splits (inversion; BTRS, Hoermann 1993), then the
  *     sampling loop inside each tile
@@ -90,6 +91,29 @@ uint64_t orc_scramble(uint64_t x, int k, const uint64_t consts[6]);
 int orc_generate_scrambled(const orc_table *const *tables, int ngroups, int k, int undirected,
                            const uint64_t *consts, uint64_t seed, uint64_t e0, uint64_t count,
                            uint64_t *row, uint64_t *col);
+
+/* Stochastic Kronecker graphs with an n0 x n0 initiator theta (Sec. 3: a
+ * k x k matrix instead of the 2 x 2 one; n0 = 2..16, row-major theta summing
+ * to 1).  Symbol s = n0 * i + j picks cell (i, j): row digit i, column digit
+ * j of the level, in base n0.  Tables as for R-MAT with n0^2 children per
+ * expansion: variable-length (expand while |Q| + n0^2 - 1 < bound, depth cap
+ * min(k, largest L with n0^L <= 2^32)) or all (n0^2)^ell paths.  Generation
+ * is the R-MAT sampling loop with base-n0 digits; n0^k <= 2^64. */
+typedef struct orc_ktable orc_ktable;
+orc_ktable *orc_kron_table_variable(const double *theta, int n0, int k, uint64_t bound);
+orc_ktable *orc_kron_table_fixed(const double *theta, int n0, int ell);
+void orc_kron_table_free(orc_ktable *t);
+int orc_kron_table_entries(const orc_ktable *t);
+int orc_kron_table_bits(const orc_ktable *t);
+int orc_kron_table_max_len(const orc_ktable *t);
+/* sym: N x max_len symbols (first level first); other arrays as orc_table_get. */
+void orc_kron_table_get(const orc_ktable *t, uint8_t *sym, uint8_t *len, double *p,
+                        uint64_t *w, uint32_t *thr, uint32_t *alias);
+uint32_t orc_kron_draw(const orc_ktable *t, uint32_t u);
+int orc_kron_generate(const orc_ktable *t, int k, uint64_t seed, uint64_t e0, uint64_t count,
+                      uint64_t *row, uint64_t *col);
+/* Exact P(row, col) over the n0^k x n0^k matrix (n0^k <= 4096). */
+int orc_kron_edge_distribution(const orc_ktable *t, int k, int quantised, double *out);
 
 /* Partitioned graphs (Sec. 3).  The 2^k x 2^k adjacency matrix is cut into
  * 2^t x 2^t tiles.  From the root (depth 0, m edges) every node (depth, R, C)

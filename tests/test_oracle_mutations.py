@@ -13,8 +13,8 @@ import test_oracle_pins as pins
 SRC = os.path.join(os.path.dirname(oracle.__file__), "rmat_oracle.c")
 
 MUTATIONS = [
-    ("b and c swapped in the expansion", "child.p = e.p * P[s];",
-     "child.p = e.p * P[s == 1 ? 2 : (s == 2 ? 1 : s)];",
+    ("b and c swapped in the expansion", "child.p = e.p * P[s];\n            child.len = e.len + 1;",
+     "child.p = e.p * P[s == 1 ? 2 : (s == 2 ? 1 : s)];\n            child.len = e.len + 1;",
      [lambda: pins.test_exact_distribution_equals_kronecker(*list(pins._distribution_cases())[5])]),
     ("row and column bits swapped", "                r = (r << 1) | (uint64_t)(s >> 1);\n                c = (c << 1) | (uint64_t)(s & 1);\n            }\n            filled += take;",
      "                r = (r << 1) | (uint64_t)(s & 1);\n                c = (c << 1) | (uint64_t)(s >> 1);\n            }\n            filled += take;",
@@ -53,6 +53,11 @@ MUTATIONS = [
      [lambda: pins.test_binomial_matches_exact_pmf(7, 0.3), lambda: pins.test_binomial_matches_exact_pmf(40, 0.2)]),
     ("BTRS candidate shifted", "const double c = nd * p + 0.5;", "const double c = nd * p + 1.5;",
      [lambda: pins.test_binomial_matches_exact_pmf(60, 0.4), lambda: pins.test_binomial_matches_exact_pmf(100, 0.5)]),
+    ("Kronecker row and column digits swapped", "r = r * n0 + (uint64_t)(s / t->n0);\n                c = c * n0 + (uint64_t)(s % t->n0);",
+     "r = r * n0 + (uint64_t)(s % t->n0);\n                c = c * n0 + (uint64_t)(s / t->n0);",
+     [pins.test_kron_generated_edges_follow_kronecker_power]),
+    ("Kronecker stop rule keeps the 2 x 2 slack", "heap.n + ndone + (size_t)(S - 1) < bound", "heap.n + ndone + 3 < bound",
+     [lambda: pins.test_kron_table_sizes_and_prefix_code(3, 104)]),
     ("tile prefix dropped", "        uint64_t r = pre_r, c = pre_c;", "        uint64_t r = pre_r, c = 0;",
      [pins.test_partitioned_graph_has_the_kronecker_distribution]),
     ("edge numbering restarts in every tile", "x->first[x->n] = x->next;", "x->first[x->n] = 0;",

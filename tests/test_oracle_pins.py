@@ -25,6 +25,7 @@ import oracle
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 G500 = (0.57, 0.19, 0.19, 0.05)
 ASYM = (0.5, 0.2, 0.25, 0.05)  # b != c, so a b/c or row/col slip shows
+SKEWED = (0.9, 0.03, 0.05, 0.02)
 
 
 def kronecker(P_levels, k):
@@ -581,3 +582,91 @@ def test_partition_depth_zero_is_the_plain_graph():
     assert list(tiles["count"]) == [5000] and list(tiles["first"]) == [0]
     r0, c0 = oracle.generate([table], 20, 77, 0, 5000)
     assert np.array_equal(r, r0) and np.array_equal(c, c0)
+
+
+# ---------------------------------------------- larger Kronecker initiators --
+
+THETA3 = np.array([[0.40, 0.15, 0.05], [0.12, 0.10, 0.04], [0.06, 0.03, 0.05]])  # asymmetric
+THETA4 = np.arange(1, 17, dtype=np.float64).reshape(4, 4)[::-1] ** 1.5
+THETA3 = THETA3 / THETA3.sum()
+THETA4 = THETA4 / THETA4.sum()
+
+
+def kron_power(theta, k):
+    """Closed form of the stochastic Kronecker graph: theta^(x k), the first
+    factor giving the most significant digit."""
+    K = np.ones((1, 1))
+    for _ in range(k):
+        K = np.kron(K, theta)
+    return K
+
+
+@pytest.mark.parametrize("kind,args", [("variable", (G500, 26, 4096)), ("variable", (ASYM, 10, 100)),
+                                       ("variable", (SKEWED, 40, 2000)), ("fixed", (ASYM, 4))])
+def test_kron_with_two_by_two_initiator_is_rmat(kind, args):
+    """n0 = 2 is R-MAT: same tables, same edges."""
+    if kind == "variable":
+        P, k, bound = args
+        kt = oracle.KronTable.variable(np.array(P).reshape(2, 2), 2, k, bound)
+        rt = oracle.Table.variable(*P, k, bound)
+    else:
+        P, ell = args
+        k = 12
+        kt = oracle.KronTable.fixed(np.array(P).reshape(2, 2), 2, ell)
+        rt = oracle.Table.fixed([P], ell)
+    for f in ("len", "p", "w", "thr", "alias"):
+        assert np.array_equal(getattr(kt, f), getattr(rt, f)), f
+    for i in range(rt.entries):
+        L = int(rt.len[i])
+        assert [int(x) for x in kt.sym[i, :L]] == [int(rt.sym[i]) >> (62 - 2 * t) & 3 for t in range(L)]
+    a, b = oracle.kron_generate(kt, k, 3, 77, 5000), oracle.generate([rt], k, 3, 77, 5000)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("theta,n0,k,kind,x", [(THETA3, 3, 3, "variable", 60), (THETA3, 3, 3, "fixed", 2),
+                                               (THETA4, 4, 2, "variable", 50), (THETA3, 3, 4, "variable", 200)])
+def test_kron_exact_distribution_equals_kronecker_power(theta, n0, k, kind, x):
+    t = oracle.KronTable.variable(theta, n0, k, x) if kind == "variable" else oracle.KronTable.fixed(theta, n0, x)
+    D = oracle.kron_edge_distribution(t, k)
+    assert np.abs(D - kron_power(theta, k)).max() <= 1e-12
+    Dq = oracle.kron_edge_distribution(t, k, quantised=True)
+    assert np.abs(Dq - kron_power(theta, k)).max() <= 8 * (1 << t.bits) * 2.0 ** -32
+
+
+@pytest.mark.parametrize("n0,bound", [(3, 104), (3, 4096), (4, 1000), (5, 4096), (16, 5000)])
+def test_kron_table_sizes_and_prefix_code(n0, bound):
+    S = n0 * n0
+    theta = np.random.default_rng(n0).dirichlet(np.ones(S)).reshape(n0, n0)
+    t = oracle.KronTable.variable(theta, n0, 12, bound)
+    assert t.entries == max(1 + (S - 1) * ((bound - 2) // (S - 1)), 1)   # largest 1 + (S-1)j < bound
+    L = t.len[:t.entries].astype(np.float64)
+    assert abs((float(S) ** -L).sum() - 1.0) < 1e-12                      # complete prefix code (Kraft)
+    assert abs(t.p[:t.entries].sum() - 1.0) < 1e-12
+    # greedy max-min: every open leaf is no likelier than every expanded node
+    leaves = {tuple(int(v) for v in t.sym[i, :int(t.len[i])]) for i in range(t.entries)}
+    internal = {lf[:j] for lf in leaves for j in range(len(lf))}
+    pr = lambda path: float(np.prod([theta.ravel()[s] for s in path]))
+    assert min(pr(n) for n in internal) >= max(pr(lf) for lf in leaves) * (1 - 1e-12)
+
+
+def test_kron_fixed_entries_are_digits_and_depth_is_capped():
+    t = oracle.KronTable.fixed(THETA3, 3, 3)
+    for j in (0, 1, 80, 729 - 1, 500):
+        assert [int(v) for v in t.sym[j, :3]] == [j // 81 % 9, j // 9 % 9, j % 9]
+    skew = np.array([[0.9, 0.02, 0.02], [0.02, 0.01, 0.01], [0.01, 0.005, 0.005]])
+    t = oracle.KronTable.variable(skew / skew.sum(), 3, 40, 1 << 16)
+    assert t.max_len == 20          # 3^20 <= 2^32 < 3^21
+
+
+def test_kron_generated_edges_follow_kronecker_power():
+    k, m = 4, 1 << 18
+    t = oracle.KronTable.variable(THETA3, 3, k, 300)
+    r, c = oracle.kron_generate(t, k, 9, 0, m)
+    nv = 3 ** k
+    counts = np.bincount(r.astype(np.int64) * nv + c.astype(np.int64), minlength=nv * nv).astype(float)
+    probs = kron_power(THETA3, k).ravel()
+    order = np.argsort(probs)
+    small = np.cumsum(probs[order] * m) < 50
+    cc = np.concatenate([[counts[order][small].sum()], counts[order][~small]])
+    pp = np.concatenate([[probs[order][small].sum()], probs[order][~small]])
+    assert _chi2_pvalue(cc, pp) > 1e-3

@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-edges", type=int, default=1 << 27)
-    ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5", "part"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5", "part", "kron"], default="c2",
                     help="c2 (default): the contract line; c1/c3/c4/c5: the other configurations, one JSON line each")
     ap.add_argument("--log2m", type=int, default=LOG2M,
                     help="c2: edges per GPU = 2^log2m (default 30; smaller only for profiling captures)")
@@ -503,6 +503,31 @@ def run_part(args):
                       "plain_single_launch_edges_per_s": m / plain_s}), flush=True)
 
 
+def run_kron(args):
+    """Stochastic Kronecker graph with a 3 x 3 initiator (Sec. 3): k = 17
+    (3^17 = 1.3e8 vertices), m = 2^30, variable table bound 4096, u32."""
+    import torch
+    import numpy as np
+    import paper_1905_03525_gb300 as rm
+    from paper_1905_03525_gb300.workloads import KRON3
+    k, m = 17, 1 << args.log2m
+    table = rm.rmat_build_table_kron(np.array(KRON3), 3, k, BOUND)
+    out = rm.empty_edges_for(table, m)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(max(3, args.warmup)):
+            rm.rmat_generate(table, SEED, 0, m, out, s)
+        dt = _events_time(lambda: rm.rmat_generate(table, SEED, 0, m, out, s), s, args.steps)
+    rm.rmat_check_device_errors()
+    peak, peak_src = measured_peak()
+    info = rm.rmat_table_info(table)
+    print(json.dumps({"workload": "kron", "config": {"workload": f"stochastic Kronecker graph, 3x3 initiator {KRON3}, "
+                      f"k={k} (3^{k} vertices), m=2^{args.log2m}, table bound {BOUND} ({info['entries']} entries), "
+                      "u32", "n0": 3, "k": k},
+                      "metric": "edges/s", "value": m / dt, "ms_per_launch": dt * 1e3,
+                      "hbm_frac": 8.0 * m / dt / 1e9 / peak, "peak_source": peak_src}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -515,6 +540,8 @@ def main():
         run_c4(args)
     elif args.workload == "part":
         run_part(args)
+    elif args.workload == "kron":
+        run_kron(args)
     elif args.workload == "c5":
         from paper_1905_03525_gb300 import serve
         serve.bench(args)

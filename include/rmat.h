@@ -122,9 +122,10 @@ typedef struct {
     int entries;        /* |Q| of group 0 (before padding) */
     int bits;           /* b of group 0: padded size 2^b */
     int max_len;        /* longest path of any group, in levels */
-    int index_bytes;    /* 4 (k <= 32) or 8 */
+    int index_bytes;    /* 4 (vertex IDs < 2^32: k <= 32, or n0^k <= 2^32) or 8 */
     unsigned flags;
     uint64_t device_image_bytes; /* size of the device copy of all groups */
+    int n0;             /* initiator size: 2 for R-MAT, n0 for rmat_build_table_kron */
 } rmat_table_info_t;
 
 rmat_status rmat_table_info(const rmat_table *t, rmat_table_info_t *info);
@@ -134,10 +135,38 @@ rmat_status rmat_table_group_info(const rmat_table *t, int group, int *entries, 
                                   int *max_len);
 
 /*
+ * Stochastic Kronecker graphs (Sec. 3: an n0 x n0 matrix instead of the 2 x 2
+ * one in the recursion).  theta: n0 x n0 initiator, row-major, entries >= 0
+ * summing to 1 (within 1e-9; divided by their sum); 2 <= n0 <= 16.  The
+ * graph has n0^k vertices (n0^k <= 2^64); level t of an edge picks initiator
+ * cell (i, j) with probability theta[i][j], i being digit t (from the most
+ * significant) of the row in base n0 and j that of the column.  Symbol
+ * s = n0 * i + j.  Tables generalise the R-MAT ones: a variable-length table
+ * expands an entry into its n0^2 children while |Q| + n0^2 - 1 < bound
+ * (largest tie-break and canonical order as for R-MAT; paths stop at min(k,
+ * L) levels, L the largest with n0^L <= 2^32); a fixed table holds all
+ * (n0^2)^ell paths.  rmat_generate and rmat_generate_host accept the table;
+ * each edge draws whole paths as for R-MAT (one Philox word per draw) and
+ * appends their base-n0 digits until k levels are filled, the last path cut
+ * to its top digits.  Output: (row, col) u32 pairs when n0^k <= 2^32, else
+ * u64 (index_bytes of rmat_table_info).  n0 = 2 builds the R-MAT table of
+ * (a, b, c, d) = (theta[0][0], theta[0][1], theta[1][0], theta[1][1]).  For
+ * n0 > 2 the table must fit in shared memory (24 bytes per column, about
+ * 9000 columns), and flags, scrambling, batches and partitions are refused
+ * (RMAT_ERR_UNSUPPORTED).
+ */
+rmat_status rmat_build_table_kron(const double *theta, int n0, int k, uint64_t table_bound,
+                                  rmat_table **out);
+rmat_status rmat_build_table_kron_fixed(const double *theta, int n0, int k, int ell,
+                                        rmat_table **out);
+
+/*
  * rmat_table_export -- copy out group `group` in canonical order (paths in
  * lexicographic order, zero-probability padding at the end), arrays of length
  * 2^bits.  sym: the path, 2 bits per level (2*rowbit + colbit), top level in
- * bits 63..62; len: levels; p: FP64 probability; w: u32 weight (held in a
+ * bits 63..62 (Kronecker tables: the symbols as base-n0^2 digits, first level
+ * most significant, left-aligned in L digits, L the depth cap of n0); len:
+ * levels; p: FP64 probability; w: u32 weight (held in a
  * uint64); thr/alias: the alias table (draw: column j = top `bits` bits of a
  * word, residual r = the rest; entry j if r < thr[j], else alias[j]).
  * Any pointer may be NULL.  Host memory.

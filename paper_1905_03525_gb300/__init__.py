@@ -23,6 +23,7 @@ __all__ = [
     "rmat_batch_add", "rmat_batch_prepare", "rmat_batch_launch", "rmat_batch_size", "rmat_batch_free",
     "rmat_generate_batch_noalloc", "rmat_batch_add_tile", "Partition", "rmat_partition_create",
     "rmat_partition_info", "rmat_partition_tiles", "rmat_generate_partition", "rmat_free_partition",
+    "rmat_build_table_kron", "rmat_build_table_kron_fixed", "empty_edges_for",
 ]
 
 
@@ -100,6 +101,19 @@ def rmat_build_table_levels(abcd, k, ell, flags=0) -> Table:
     return _new_table(lambda out: lib().rmat_build_table_levels(P.ctypes.data, k, ell, flags, out))
 
 
+def rmat_build_table_kron(theta, n0, k, table_bound) -> Table:
+    """Stochastic Kronecker graph with an n0 x n0 initiator (Sec. 3):
+    variable-length table of similar-probability paths."""
+    th = np.ascontiguousarray(theta, dtype=np.float64).reshape(n0 * n0)
+    return _new_table(lambda out: lib().rmat_build_table_kron(th.ctypes.data, n0, k, table_bound, out))
+
+
+def rmat_build_table_kron_fixed(theta, n0, k, ell) -> Table:
+    """Stochastic Kronecker graph: all (n0^2)^ell paths of length ell."""
+    th = np.ascontiguousarray(theta, dtype=np.float64).reshape(n0 * n0)
+    return _new_table(lambda out: lib().rmat_build_table_kron_fixed(th.ctypes.data, n0, k, ell, out))
+
+
 def rmat_table_set_flags(t: Table, flags: int) -> None:
     check(lib().rmat_table_set_flags(t.handle, flags))
 
@@ -150,6 +164,15 @@ def empty_edges(count: int, k: int, device="cuda", pin_memory=False):
     (count, 2), uint32 (k <= 32) or int64 holding uint64 bits (k > 32)."""
     import torch
     dt = torch.int32 if k <= 32 else torch.int64
+    if device == "cpu":
+        return torch.empty((count, 2), dtype=dt, pin_memory=pin_memory)
+    return torch.empty((count, 2), dtype=dt, device=device)
+
+
+def empty_edges_for(t: Table, count: int, device="cuda", pin_memory=False):
+    """Output buffer for `count` edges of table t (its vertex-ID width)."""
+    import torch
+    dt = torch.int32 if rmat_table_info(t)["index_bytes"] == 4 else torch.int64
     if device == "cpu":
         return torch.empty((count, 2), dtype=dt, pin_memory=pin_memory)
     return torch.empty((count, 2), dtype=dt, device=device)

@@ -33,7 +33,7 @@ class RmatError(RuntimeError):
 class TableInfo(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("groups", ctypes.c_int), ("entries", ctypes.c_int),
                 ("bits", ctypes.c_int), ("max_len", ctypes.c_int), ("index_bytes", ctypes.c_int),
-                ("flags", ctypes.c_uint), ("device_image_bytes", ctypes.c_uint64)]
+                ("flags", ctypes.c_uint), ("device_image_bytes", ctypes.c_uint64), ("n0", ctypes.c_int)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -79,6 +79,8 @@ SIGNATURES = [
     ("rmat_build_table_levels", _st, [_vp, _i32, _i32, _u32, _vp]),
     ("rmat_table_set_flags", _st, [_vp, _u32]),
     ("rmat_table_set_scramble", _st, [_vp, _i32, _u64]),
+    ("rmat_build_table_kron", _st, [_vp, _i32, _i32, _u64, _vp]),
+    ("rmat_build_table_kron_fixed", _st, [_vp, _i32, _i32, _i32, _vp]),
     ("rmat_batch_add_tile", _st, [_vp, _vp, _u64, _u64, _u64, _i32, _u64, _u64, _vp]),
     ("rmat_partition_create", _st, [_vp, _i32, _u64, _u64, _u64, _u64, _vp]),
     ("rmat_partition_info", _st, [_vp, _vp, _vp]),

@@ -79,7 +79,7 @@ rmat_status check_generate_args(const rmat_table *t, uint64_t edge_offset, uint6
     if (reinterpret_cast<uintptr_t>(out) & 7u) return fail(RMAT_ERR_INVALID_ARGUMENT, "output must be 8-byte aligned");
     if (count > ~uint64_t(0) - edge_offset)
         return fail(RMAT_ERR_INVALID_ARGUMENT, "edge_offset + count overflows 64 bits");
-    const uint64_t eb = t->k > 32 ? 16 : 8;
+    const uint64_t eb = wide_ids(t) ? 16 : 8;
     if (count > (~uint64_t(0)) / eb) return fail(RMAT_ERR_INVALID_ARGUMENT, "count too large");
     return RMAT_OK;
 }
@@ -208,6 +208,66 @@ rmat_status rmat_build_table_fixed(double a, double b, double c, double d, int k
     return finish_table(t, out);
 }
 
+rmat_status rmat_build_table_kron(const double *theta, int n0, int k, uint64_t table_bound, rmat_table **out) {
+    clear_error();
+    if (!out) return fail(RMAT_ERR_INVALID_ARGUMENT, "out is NULL");
+    *out = nullptr;
+    if (!theta) return fail(RMAT_ERR_INVALID_ARGUMENT, "theta is NULL");
+    if (n0 < 2 || n0 > 16) return fail(RMAT_ERR_INVALID_ARGUMENT, "n0 must be in [2, 16]");
+    if (n0 == 2) return rmat_build_table(theta[0], theta[1], theta[2], theta[3], k, table_bound, out);
+    if (k < 1 || k > kron_max_k(n0)) return fail(RMAT_ERR_INVALID_ARGUMENT, "k must satisfy 1 <= k and n0^k <= 2^64");
+    if (table_bound < uint64_t(n0) * n0 + 1 || table_bound > (uint64_t(1) << 24))
+        return fail(RMAT_ERR_INVALID_ARGUMENT, "table_bound must be in [n0^2 + 1, 2^24]");
+    std::vector<double> P;
+    if (rmat_status st = normalise_theta(theta, n0, P)) return st;
+    rmat_table *t = new (std::nothrow) rmat_table;
+    if (!t) return fail(RMAT_ERR_OUT_OF_MEMORY, "host allocation failed");
+    t->k = k;
+    t->n0 = n0;
+    t->groups.resize(1);
+    try {
+        if (rmat_status st = build_kron_variable(P.data(), n0, k, table_bound, t->groups[0])) {
+            delete t;
+            return st;
+        }
+    } catch (const std::bad_alloc &) {
+        delete t;
+        return fail(RMAT_ERR_OUT_OF_MEMORY, "host allocation failed");
+    }
+    return finish_table(t, out);
+}
+
+rmat_status rmat_build_table_kron_fixed(const double *theta, int n0, int k, int ell, rmat_table **out) {
+    clear_error();
+    if (!out) return fail(RMAT_ERR_INVALID_ARGUMENT, "out is NULL");
+    *out = nullptr;
+    if (!theta) return fail(RMAT_ERR_INVALID_ARGUMENT, "theta is NULL");
+    if (n0 < 2 || n0 > 16) return fail(RMAT_ERR_INVALID_ARGUMENT, "n0 must be in [2, 16]");
+    if (n0 == 2) return rmat_build_table_fixed(theta[0], theta[1], theta[2], theta[3], k, ell, out);
+    if (k < 1 || k > kron_max_k(n0)) return fail(RMAT_ERR_INVALID_ARGUMENT, "k must satisfy 1 <= k and n0^k <= 2^64");
+    double entries = 1.0;
+    for (int i = 0; i < ell; ++i) entries *= double(n0) * n0;
+    if (ell < 1 || ell > kron_depth_cap(n0) || entries > double(1 << 24))
+        return fail(RMAT_ERR_INVALID_ARGUMENT, "ell must be >= 1 with (n0^2)^ell <= 2^24");
+    std::vector<double> P;
+    if (rmat_status st = normalise_theta(theta, n0, P)) return st;
+    rmat_table *t = new (std::nothrow) rmat_table;
+    if (!t) return fail(RMAT_ERR_OUT_OF_MEMORY, "host allocation failed");
+    t->k = k;
+    t->n0 = n0;
+    t->groups.resize(1);
+    try {
+        if (rmat_status st = build_kron_fixed(P.data(), n0, ell, t->groups[0])) {
+            delete t;
+            return st;
+        }
+    } catch (const std::bad_alloc &) {
+        delete t;
+        return fail(RMAT_ERR_OUT_OF_MEMORY, "host allocation failed");
+    }
+    return finish_table(t, out);
+}
+
 rmat_status rmat_build_table_levels(const double *abcd, int k, int ell, unsigned flags, rmat_table **out) {
     clear_error();
     if (!out) return fail(RMAT_ERR_INVALID_ARGUMENT, "out is NULL");
@@ -245,6 +305,7 @@ rmat_status rmat_table_set_flags(rmat_table *t, unsigned flags) {
     clear_error();
     if (!t) return fail(RMAT_ERR_INVALID_ARGUMENT, "table is NULL");
     if (flags & ~RMAT_UNDIRECTED) return fail(RMAT_ERR_INVALID_ARGUMENT, "unknown flag");
+    if (flags && t->n0 > 2) return fail(RMAT_ERR_UNSUPPORTED, "Kronecker tables (n0 > 2) take no flags");
     t->flags = flags;
     return RMAT_OK;
 }
@@ -252,6 +313,7 @@ rmat_status rmat_table_set_flags(rmat_table *t, unsigned flags) {
 rmat_status rmat_table_set_scramble(rmat_table *t, int enable, uint64_t scramble_seed) {
     clear_error();
     if (!t) return fail(RMAT_ERR_INVALID_ARGUMENT, "table is NULL");
+    if (enable && t->n0 > 2) return fail(RMAT_ERR_UNSUPPORTED, "Kronecker tables (n0 > 2) are not scrambled");
     std::lock_guard<std::mutex> lk(t->mu);
     t->scramble = enable != 0;
     if (t->scramble) {
@@ -282,7 +344,8 @@ rmat_status rmat_table_info(const rmat_table *t, rmat_table_info_t *info) {
     int ml = 0;
     for (const PathTable &g : t->groups) ml = std::max(ml, g.max_len);
     info->max_len = ml;
-    info->index_bytes = t->k > 32 ? 8 : 4;
+    info->index_bytes = wide_ids(t) ? 8 : 4;
+    info->n0 = t->n0;
     info->flags = t->flags;
     info->device_image_bytes = uint64_t(t->image.size()) * 4;
     return RMAT_OK;
@@ -377,7 +440,7 @@ rmat_status rmat_generate_host(const rmat_table *t, uint64_t seed, uint64_t edge
     if (rmat_status st = ensure_device_copy(t, &img)) return st;
     HostStaging *s = nullptr;
     if (rmat_status st = get_staging(s)) return st;
-    const uint64_t eb = t->k > 32 ? 16 : 8;
+    const uint64_t eb = wide_ids(t) ? 16 : 8;
     const uint64_t chunk = s->bytes / eb;
     cudaError_t e;
     uint64_t done = 0;

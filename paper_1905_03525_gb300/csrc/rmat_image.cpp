@@ -44,7 +44,53 @@ size_t round16w(size_t words) { return (words + 3) & ~size_t(3); }
 
 }  // namespace
 
+// Kronecker tables (n0 > 2, one group): after the header,
+//   AA[j] uint2 {A[j], alias[j]}   (A as above)
+//   P[j]  uint4 {row digits, column digits, L, n0^L - 1}
+// where the digits of the path's L levels are read as base-n0 numbers (both
+// < n0^L <= 2^32); the kernel appends a path as x = x * n0^L + digits, i.e.
+// x * (n0^L - 1) + x + digits, which keeps n0^L = 2^32 within 32 bits.
+// Header word g is the AA offset, 64 + g the P offset, 192 + g = b.
+rmat_status build_kron_image(rmat_table *t) {
+    const PathTable &g = t->groups[0];
+    const size_t N = size_t(1) << g.bits;
+    GroupDesc d;
+    d.a_off_words = uint32_t(kHeaderWords);
+    d.bs_off_words = uint32_t(kHeaderWords + round16w(2 * N));
+    d.ba_off_words = 0;
+    d.bits = g.bits;
+    d.len = g.max_len;
+    t->format = kKron;
+    t->gdesc.assign(1, d);
+    t->image.assign(round16w(d.bs_off_words + 4 * N), 0u);
+    t->image[0] = d.a_off_words;
+    t->image[kMaxGroups] = d.bs_off_words;
+    t->image[3 * kMaxGroups] = uint32_t(g.bits);
+    const uint32_t C = uint32_t((uint64_t(1) << 32) >> g.bits);
+    const uint64_t n0 = uint64_t(t->n0);
+    uint32_t *AA = t->image.data() + d.a_off_words;
+    uint32_t *P = t->image.data() + d.bs_off_words;
+    for (size_t j = 0; j < N; ++j) {
+        AA[2 * j] = uint32_t(j) * C + g.thr[j];
+        AA[2 * j + 1] = g.alias[j];
+        const int L = g.len[j];
+        uint64_t r = 0, c = 0, pw = 1;
+        for (int lvl = 0; lvl < L; ++lvl) {
+            const uint32_t s = kron_symbol(g.sym[j], t->n0, lvl);
+            r = r * n0 + s / n0;
+            c = c * n0 + s % n0;
+            pw *= n0;
+        }
+        P[4 * j + 0] = uint32_t(r);
+        P[4 * j + 1] = uint32_t(c);
+        P[4 * j + 2] = uint32_t(L);
+        P[4 * j + 3] = uint32_t(pw - 1);
+    }
+    return RMAT_OK;
+}
+
 rmat_status build_image(rmat_table *t) {
+    if (t->n0 > 2) return build_kron_image(t);
     int max_len = 0;
     for (const PathTable &g : t->groups) max_len = std::max(max_len, g.max_len);
     if (max_len > 32) return fail(RMAT_ERR_UNSUPPORTED, "paths longer than 32 levels");

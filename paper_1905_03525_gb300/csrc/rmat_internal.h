@@ -14,11 +14,14 @@ namespace rmat {
 // One alias table: the canonical list of paths plus its alias structure
 // (one per level group for per-level tables).
 struct PathTable {
+    int n0 = 2;                    // initiator size: symbols are the n0^2 cells
     int entries = 0;               // |Q|
     int bits = 0;                  // b, padded size N = 2^b
     int max_len = 0;               // longest path (levels)
     int min_len = 0;               // shortest path with non-zero weight
-    std::vector<uint64_t> sym;     // path symbols, top level in bits 63..62
+    std::vector<uint64_t> sym;     // path symbols, top level in bits 63..62 (n0 = 2);
+                                   // n0 > 2: base-n0^2 digits, left-aligned in
+                                   // kron_depth_cap(n0) digits (kron_symbol)
     std::vector<uint8_t> len;      // path length (levels)
     std::vector<double> p;         // FP64 path probability
     std::vector<uint64_t> w;       // u32 weight, sum 2^32
@@ -32,7 +35,8 @@ constexpr size_t kHeaderWords = 4 * kMaxGroups; // blob header: A, B-self, B-ali
 // Device table image formats (see rmat_image.cpp).
 enum ImageFormat : int {
     kCompact = 0,  // paths <= 13 levels: A = (thr << b) | alias (u32), B = packed path (u32)
-    kWide = 1      // paths <= 32 levels: A as above, B = {row bits, col bits, len, 0} (uint4)
+    kWide = 1,     // paths <= 32 levels: A as above, B = {row bits, col bits, len, 0} (uint4)
+    kKron = 2      // n0 > 2: AA = {A, alias} (uint2), P = {row digits, col digits, len, n0^len - 1} (uint4)
 };
 
 struct GroupDesc {
@@ -67,6 +71,7 @@ struct AliasPlan {
 
 struct rmat_table {
     int k = 0;
+    int n0 = 2;                             // initiator size (2 = R-MAT)
     unsigned flags = 0;
     bool per_level = false;                 // draw g uses group g
     std::vector<rmat::PathTable> groups;
@@ -92,6 +97,16 @@ void clear_error();
 
 // Table construction (rmat_table.cpp).
 rmat_status build_variable(const double P[4], int k, uint64_t bound, PathTable &out);
+// Stochastic Kronecker tables with an n0 x n0 initiator P (row-major, normalised).
+rmat_status build_kron_variable(const double *P, int n0, int k, uint64_t bound, PathTable &out);
+rmat_status build_kron_fixed(const double *P, int n0, int ell, PathTable &out);
+rmat_status normalise_theta(const double *in, int n0, std::vector<double> &out);
+int kron_depth_cap(int n0);   // largest L with n0^L <= 2^32
+int kron_max_k(int n0);       // largest k with n0^k <= 2^64
+// Symbol of `level` in the left-aligned base-n0^2 key of a Kronecker path.
+uint32_t kron_symbol(uint64_t key, int n0, int level);
+// Whether the table's vertex IDs need 64 bits (n0^k > 2^32).
+bool wide_ids(const rmat_table *t);
 rmat_status build_fixed(const double *P_levels, int ell, PathTable &out);
 rmat_status normalise_params(const double in[4], double out[4]);
 

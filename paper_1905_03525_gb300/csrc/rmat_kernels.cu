@@ -514,6 +514,66 @@ __global__ void __launch_bounds__(1024) k_batch(BatchArgs B) {
     if (lane == 0 && W.issued) dev::bulk_wait_all();
 }
 
+// Stochastic Kronecker graphs with an n0 x n0 initiator, n0 > 2 (Sec. 3).
+// One edge per thread over a persistent grid: the table (AA = {A, alias},
+// P = {row digits, column digits, L, n0^L - 1}) is staged in shared memory,
+// each draw picks column j = umulhi(u, 2^b), keeps it iff u < A[j] (else its
+// alias), and appends the path's digits in base n0; the draw that would pass
+// k levels keeps only the path's top k - filled digits (floor division by
+// n0^d as a multiply-high).  Every draw adds >= 1 level (zero-weight columns
+// always defer to their alias), so k <= 40 levels need <= 10 blocks.
+template <bool U64>
+__global__ void __launch_bounds__(1024, 1) k_kron(const __grid_constant__ KronJob J) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const uint4 *src = reinterpret_cast<const uint4 *>(J.blob);
+    uint4 *dst = reinterpret_cast<uint4 *>(smem);
+    for (uint32_t i = threadIdx.x; i < J.blob_bytes / 16; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    using Word = typename AccT<U64>::word;
+    const uint32_t sAA = dev::smem_u32(smem) + J.aa_off;
+    const uint32_t sP = dev::smem_u32(smem) + J.p_off;
+    const uint32_t uk = uint32_t(J.k);
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < J.count; i += stride) {
+        const uint64_t e = J.e0 + i;
+        Word row = 0, col = 0;
+        uint32_t filled = 0;
+        auto draw = [&](uint32_t u) {
+            const uint32_t j = __umulhi(u, J.mulb);
+            const uint2 aa = dev::lds64(sAA + 8u * j);
+            const uint4 p = dev::lds128(sP + 16u * (u < aa.x ? j : aa.y));
+            if (filled + p.z <= uk) {
+                row = row * Word(p.w) + row + Word(p.x);  // row * n0^L + digits
+                col = col * Word(p.w) + col + Word(p.y);
+                filled += p.z;
+            } else {
+                const uint32_t take = uk - filled, d = p.z - take;
+                row = row * Word(J.pw[take]) + Word(__umul64hi(uint64_t(p.x), J.mg[d]));
+                col = col * Word(J.pw[take]) + Word(__umul64hi(uint64_t(p.y), J.mg[d]));
+                filled = uk;
+            }
+        };
+        for (uint32_t q = 0; q < 16 && filled < uk; ++q) {
+            const uint4 w = dev::philox_ks(q, 0u, uint32_t(e), uint32_t(e >> 32), J.ks);
+            draw(w.x);
+            if (filled >= uk) break;
+            draw(w.y);
+            if (filled >= uk) break;
+            draw(w.z);
+            if (filled >= uk) break;
+            draw(w.w);
+        }
+        if constexpr (U64) {
+            // outputs are only 8-byte aligned: two 8-byte stores
+            uint64_t *o = reinterpret_cast<uint64_t *>(J.out) + 2 * i;
+            o[0] = row;
+            o[1] = col;
+        } else {
+            reinterpret_cast<uint2 *>(J.out)[i] = make_uint2(row, col);
+        }
+    }
+}
+
 // Order-independent checksum of the edges of every job of a step: the sum
 // mod 2^64 of mix(e, row, col) over the job's edges, where
 //   x = e * 0x9E3779B97F4A7C15 + row * 0xC2B2AE3D27D4EB4F + col * 0x165667B19E3779F9
@@ -686,9 +746,71 @@ rmat_launch_config_t default_launch_config(const rmat_table *t) {
 
 size_t warp_bytes(bool u64, bool levels, int tile) { return warp_region_bytes(u64, levels, tile); }
 
+rmat_status plan_kron_launch(const rmat_table *t, const DeviceProps &props, AliasPlan &plan) {
+    const bool u64 = wide_ids(t);
+    plan.fmt = kKron;
+    plan.u64 = u64;
+    plan.levels = false;
+    plan.smem_table = true;
+    plan.threads = 1024;
+    plan.tile = 0;
+    plan.smem_bytes = t->image.size() * 4;
+    if (plan.smem_bytes > size_t(props.max_smem))
+        return fail(RMAT_ERR_UNSUPPORTED, "Kronecker table larger than shared memory (use a smaller bound)");
+    plan.kernel = u64 ? reinterpret_cast<void *>(&k_kron<true>) : reinterpret_cast<void *>(&k_kron<false>);
+    cudaError_t e = set_smem_attr(plan.kernel, plan.smem_bytes);
+    if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan.kernel, plan.threads, plan.smem_bytes);
+    if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
+    if (per_sm < 1) return fail(RMAT_ERR_UNSUPPORTED, "launch shape does not fit on an SM");
+    plan.ctas_per_sm = per_sm;
+    plan.sms = props.sms;
+    plan.err = props.err;
+    return RMAT_OK;
+}
+
+rmat_status launch_kron(const rmat_table *t, const uint32_t *dblob, const AliasPlan &plan, uint64_t seed,
+                        uint64_t e0, uint64_t count, void *out, cudaStream_t stream) {
+    KronJob J{};
+    J.blob = dblob;
+    J.blob_bytes = uint32_t(t->image.size() * 4);
+    J.aa_off = 4u * t->gdesc[0].a_off_words;
+    J.p_off = 4u * t->gdesc[0].bs_off_words;
+    J.mulb = 1u << t->gdesc[0].bits;
+    J.k = t->k;
+    const uint32_t k0 = uint32_t(seed), k1 = uint32_t(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        J.ks[2 * r] = k0 + uint32_t(r) * 0x9E3779B9u;
+        J.ks[2 * r + 1] = k1 + uint32_t(r) * 0xBB67AE85u;
+    }
+    J.e0 = e0;
+    J.count = count;
+    J.out = out;
+    uint64_t v = 1;
+    for (int j = 0; j <= kMaxKronK; ++j) {
+        J.pw[j] = j <= t->k ? v : 0;  // n0^k may be 2^64 (wraps to 0; used only times 0)
+        v *= uint64_t(t->n0);
+    }
+    unsigned __int128 D = 1;
+    for (int d = 0; d <= 32; ++d) {
+        J.mg[d] = (d >= 1 && D <= (unsigned __int128)(uint64_t(1) << 32))
+                      ? uint64_t(((unsigned __int128)1 << 64) / D) + 1
+                      : 0;
+        D *= uint64_t(t->n0);
+    }
+    const uint64_t blocks = (count + plan.threads - 1) / plan.threads;
+    const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(blocks, uint64_t(plan.sms) * plan.ctas_per_sm)));
+    void *params[] = {&J};
+    cudaError_t e = cudaLaunchKernel(plan.kernel, dim3(grid), dim3(plan.threads), params, plan.smem_bytes, stream);
+    if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return RMAT_OK;
+}
+
 rmat_status plan_alias_launch(const rmat_table *t, const rmat_launch_config_t &want, AliasPlan &plan) {
     DeviceProps props;
     if (rmat_status st = device_props(props)) return st;
+    if (t->n0 > 2) return plan_kron_launch(t, props, plan);
     const bool u64 = t->k > 32;
     const bool levels = t->per_level;
     const size_t img = t->image.size() * 4;
@@ -797,6 +919,7 @@ Scramble make_scramble(const rmat_table *t) {
 rmat_status launch_alias(const rmat_table *t, const uint32_t *dblob, const AliasPlan &plan, uint64_t seed,
                          uint64_t e0, uint64_t count, void *out, cudaStream_t stream) {
     if (count == 0) return RMAT_OK;
+    if (plan.fmt == kKron) return launch_kron(t, dblob, plan, seed, e0, count, out, stream);
     Job J = make_job(t, dblob, plan.smem_table, seed, e0, count, out);
     Scramble S = make_scramble(t);
     unsigned *err = plan.err;

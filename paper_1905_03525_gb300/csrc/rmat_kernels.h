@@ -67,6 +67,21 @@ struct BatchArgs {
     int prefixed;              // some job is a partition tile (pre_len > 0)
 };
 
+// One launch of the Kronecker kernel (n0 > 2): edges e0 .. e0+count-1.
+constexpr int kMaxKronK = 40;  // n0 >= 3: n0^k <= 2^64
+struct KronJob {
+    const uint32_t *blob;  // device image (header, AA, P)
+    uint32_t blob_bytes;
+    uint32_t aa_off, p_off;  // byte offsets of AA and P in the image
+    uint32_t mulb;           // 2^b: column j = umulhi(u, 2^b)
+    int k;
+    uint32_t ks[20];         // Philox round keys of the seed
+    uint64_t e0, count;
+    void *out;
+    uint64_t pw[kMaxKronK + 1];  // n0^j
+    uint64_t mg[33];             // floor(2^64 / n0^d) + 1: floor(x / n0^d) = umul64hi(x, mg[d]) for x < 2^32
+};
+
 rmat_status device_props(DeviceProps &out);
 rmat_launch_config_t default_launch_config(const rmat_table *t);
 rmat_status plan_alias_launch(const rmat_table *t, const rmat_launch_config_t &want, AliasPlan &plan);

@@ -68,6 +68,8 @@ extern "C" rmat_status rmat_generate_batch_noalloc(const rmat_table *const *tabl
     bool u64 = false;
     for (uint32_t i = 0; i < n; ++i) {
         if (!tables[i]) return fail(RMAT_ERR_INVALID_ARGUMENT, "NULL table");
+        if (tables[i]->n0 > 2)
+            return fail(RMAT_ERR_UNSUPPORTED, "Kronecker tables (n0 > 2) are generated by rmat_generate only");
         if (counts[i] && !outs[i]) return fail(RMAT_ERR_INVALID_ARGUMENT, "NULL output pointer");
         if (reinterpret_cast<uintptr_t>(outs[i]) & 7u)
             return fail(RMAT_ERR_INVALID_ARGUMENT, "output must be 8-byte aligned");

@@ -158,6 +158,149 @@ rmat_status build_variable(const double P[4], int k, uint64_t bound, PathTable &
     return quantise_alias(t);
 }
 
+int kron_depth_cap(int n0) {
+    int L = 0;
+    double v = 1.0;
+    while (v * n0 <= 4294967296.0) {
+        v *= n0;
+        ++L;
+    }
+    return L;
+}
+
+int kron_max_k(int n0) {
+    int k = 0;
+    double v = 1.0;
+    while (v * n0 <= 18446744073709551616.0) {
+        v *= n0;
+        ++k;
+    }
+    return k;
+}
+
+bool wide_ids(const rmat_table *t) {
+    if (t->n0 == 2) return t->k > 32;
+    double v = 1.0;
+    for (int i = 0; i < t->k; ++i) v *= t->n0;
+    return v > 4294967296.0;
+}
+
+namespace {
+
+// Place value of the symbol at `level` in a left-aligned key of
+// kron_depth_cap(n0) base-S digits (S = n0^2): S^(D - 1 - level).  S^D =
+// n0^(2D) <= 2^64, so every key fits 64 bits; for n0 = 2 this is the R-MAT
+// layout (2 bits per level, top level in bits 63..62).
+std::vector<uint64_t> kron_places(int n0) {
+    const int D = kron_depth_cap(n0);
+    const uint64_t S = uint64_t(n0) * uint64_t(n0);
+    std::vector<uint64_t> place(D);
+    uint64_t v = 1;
+    for (int lvl = D - 1; lvl >= 0; --lvl) {
+        place[lvl] = v;
+        if (lvl) v *= S;
+    }
+    return place;
+}
+
+}  // namespace
+
+uint32_t kron_symbol(uint64_t key, int n0, int level) {
+    const uint64_t S = uint64_t(n0) * uint64_t(n0);
+    return uint32_t((key / kron_places(n0)[level]) % S);
+}
+
+rmat_status normalise_theta(const double *in, int n0, std::vector<double> &out) {
+    const int S = n0 * n0;
+    double s = 0.0;
+    for (int i = 0; i < S; ++i) {
+        if (!std::isfinite(in[i]) || in[i] < 0.0)
+            return fail(RMAT_ERR_INVALID_ARGUMENT, "initiator entries must be finite and non-negative");
+        s = s + in[i];
+    }
+    if (!(std::fabs(s - 1.0) <= 1e-9)) return fail(RMAT_ERR_INVALID_ARGUMENT, "initiator must sum to 1 (within 1e-9)");
+    out.resize(S);
+    for (int i = 0; i < S; ++i) out[i] = in[i] / s;
+    return RMAT_OK;
+}
+
+// Kronecker generalisation of build_variable (Sec. 3: an n0 x n0 initiator):
+// an expansion adds the n0^2 children, the loop runs while |Q| + n0^2 - 1 <
+// bound, and paths stop at min(k, kron_depth_cap(n0)) levels.
+rmat_status build_kron_variable(const double *P, int n0, int k, uint64_t bound, PathTable &t) {
+    const int S = n0 * n0;
+    const int cap = std::min(k, kron_depth_cap(n0));
+    const std::vector<uint64_t> place = kron_places(n0);
+    std::priority_queue<Candidate, std::vector<Candidate>, PopOrder> q;
+    std::vector<Candidate> final_entries;
+    q.push({1.0, 0, 0});
+    while (!q.empty() && q.size() + final_entries.size() + uint64_t(S - 1) < bound) {
+        const Candidate top = q.top();
+        q.pop();
+        for (int s = 0; s < S; ++s) {
+            Candidate ch{top.p * P[s], top.path + uint64_t(s) * place[top.depth], top.depth + 1};
+            if (ch.depth >= cap)
+                final_entries.push_back(ch);
+            else
+                q.push(ch);
+        }
+    }
+    while (!q.empty()) {
+        final_entries.push_back(q.top());
+        q.pop();
+    }
+    std::sort(final_entries.begin(), final_entries.end(),
+              [](const Candidate &x, const Candidate &y) { return x.path < y.path; });
+    t.n0 = n0;
+    t.entries = int(final_entries.size());
+    t.bits = bits_for(final_entries.size());
+    const size_t N = size_t(1) << t.bits;
+    t.sym.assign(N, 0);
+    t.len.assign(N, 0);
+    t.p.assign(N, 0.0);
+    t.max_len = 0;
+    for (size_t i = 0; i < final_entries.size(); ++i) {
+        t.sym[i] = final_entries[i].path;
+        t.len[i] = uint8_t(final_entries[i].depth);
+        t.p[i] = final_entries[i].p;
+        t.max_len = std::max(t.max_len, final_entries[i].depth);
+    }
+    return quantise_alias(t);
+}
+
+// All (n0^2)^ell paths; entry i has the base-n0^2 digits of i as symbols.
+rmat_status build_kron_fixed(const double *P, int n0, int ell, PathTable &t) {
+    const size_t S = size_t(n0) * size_t(n0);
+    const std::vector<uint64_t> place = kron_places(n0);
+    std::vector<double> prob(1, 1.0), next;
+    std::vector<uint64_t> path(1, 0), next_path;
+    for (int lvl = 0; lvl < ell; ++lvl) {
+        next.resize(prob.size() * S);
+        next_path.resize(prob.size() * S);
+        for (size_t i = 0; i < prob.size(); ++i)
+            for (size_t s = 0; s < S; ++s) {
+                next[S * i + s] = prob[i] * P[s];
+                next_path[S * i + s] = path[i] + uint64_t(s) * place[lvl];
+            }
+        prob.swap(next);
+        path.swap(next_path);
+    }
+    t.n0 = n0;
+    t.entries = int(prob.size());
+    t.bits = bits_for(prob.size());
+    const size_t N = size_t(1) << t.bits;
+    t.max_len = ell;
+    t.sym.assign(N, 0);
+    t.len.assign(N, 0);
+    t.p.assign(N, 0.0);
+    for (size_t i = 0; i < prob.size(); ++i) {
+        t.p[i] = prob[i];
+        t.sym[i] = path[i];
+        t.len[i] = uint8_t(ell);
+    }
+    return quantise_alias(t);
+}
+
 rmat_status build_fixed(const double *P, int ell, PathTable &t) {
     const size_t N = size_t(1) << (2 * ell);
     t.entries = int(N);

@@ -48,3 +48,9 @@ def served_trace(n: int, rate: float = 2000.0, seed: int = 2000, k_range=(12, 30
     P = rng.dirichlet(alpha, size=n)
     return [{"arrival": float(t[i]), "k": int(ks[i]), "ef": int(efs[i]), "m": int(efs[i]) << int(ks[i]),
              "abcd": tuple(float(x) for x in P[i]), "seed": int(seed + i)} for i in range(n)]
+
+
+# A 3 x 3 initiator for stochastic Kronecker graphs (Sec. 3): skewed toward
+# the first cell like the Graph 500 2 x 2 parameters, rows and columns not
+# symmetric.
+KRON3 = ((0.40, 0.15, 0.05), (0.12, 0.10, 0.04), (0.06, 0.03, 0.05))

@@ -206,3 +206,76 @@ def test_partition_host_checks():
         rm.rmat_batch_add_tile(b, lv, 1, 0, 10, 5, 0, 0, 8)    # per-level table
     rm.rmat_batch_add_tile(b, t, 1, 0, 10, 4, 15, 3, 8)
     assert rm.rmat_batch_size(b) == (1, 10)
+
+
+THETA3 = np.array([[0.40, 0.15, 0.05], [0.12, 0.10, 0.04], [0.06, 0.03, 0.05]])
+THETA3 = THETA3 / THETA3.sum()
+
+
+def _theta(n0, seed):
+    th = np.random.default_rng(seed).dirichlet(np.linspace(4.0, 0.5, n0 * n0)).reshape(n0, n0)
+    return th / th.sum()
+
+
+def _kron_digits(key, n0, L):
+    """Symbols of a library Kronecker path key (base-n0^2 digits, left-aligned
+    in D digits, D = the largest with n0^D <= 2^32)."""
+    S, D = n0 * n0, 0
+    while n0 ** (D + 1) <= 2 ** 32:
+        D += 1
+    return [int(key) // S ** (D - 1 - t) % S for t in range(L)]
+
+
+@pytest.mark.parametrize("n0,k,kind,x", [(3, 12, "variable", 500), (3, 40, "variable", 4096), (4, 10, "fixed", 2),
+                                         (5, 13, "variable", 4096), (16, 8, "variable", 5000), (3, 7, "fixed", 3)])
+def test_kron_table_matches_oracle(n0, k, kind, x):
+    th = THETA3 if n0 == 3 else _theta(n0, n0)
+    if kind == "variable":
+        t, ot = rm.rmat_build_table_kron(th, n0, k, x), oracle.KronTable.variable(th, n0, k, x)
+    else:
+        t, ot = rm.rmat_build_table_kron_fixed(th, n0, k, x), oracle.KronTable.fixed(th, n0, x)
+    ex = rm.rmat_table_export(t)
+    assert ex["entries"] == ot.entries and ex["bits"] == ot.bits and ex["max_len"] == ot.max_len
+    for f in ("len", "p", "w", "thr", "alias"):
+        assert np.array_equal(ex[f], getattr(ot, f)), f
+    for i in range(ot.entries):
+        L = int(ot.len[i])
+        assert _kron_digits(ex["sym"][i], n0, L) == [int(v) for v in ot.sym[i, :L]]
+    info = rm.rmat_table_info(t)
+    assert info["n0"] == n0
+    assert info["index_bytes"] == (4 if n0 ** k <= 2 ** 32 else 8)
+    N = 1 << ot.bits
+    assert info["device_image_bytes"] == 4 * (256 + 2 * N + 4 * N)
+
+
+def test_kron_two_by_two_is_the_rmat_table():
+    th = np.array([[0.57, 0.19], [0.19, 0.05]])
+    a, b = rm.rmat_build_table_kron(th, 2, 26, 4096), rm.rmat_build_table(0.57, 0.19, 0.19, 0.05, 26, 4096)
+    ea, eb = rm.rmat_table_export(a), rm.rmat_table_export(b)
+    assert all(np.array_equal(ea[f], eb[f]) for f in ("sym", "len", "p", "w", "thr", "alias"))
+    assert rm.rmat_table_info(a)["n0"] == 2
+
+
+def test_kron_host_checks():
+    with pytest.raises(rm.RmatError):
+        rm.rmat_build_table_kron(np.ones(1), 1, 5, 100)
+    with pytest.raises(rm.RmatError):
+        rm.rmat_build_table_kron(np.ones(289) / 289, 17, 5, 1000)
+    with pytest.raises(rm.RmatError):
+        rm.rmat_build_table_kron(THETA3, 3, 41, 100)          # 3^41 > 2^64
+    with pytest.raises(rm.RmatError):
+        rm.rmat_build_table_kron(THETA3, 3, 10, 9)            # bound < n0^2 + 1
+    with pytest.raises(rm.RmatError):
+        rm.rmat_build_table_kron(THETA3 * 1.1, 3, 10, 100)    # does not sum to 1
+    with pytest.raises(rm.RmatError):
+        rm.rmat_build_table_kron_fixed(THETA3, 3, 10, 9)      # 9^9 > 2^24 entries
+    t = rm.rmat_build_table_kron(THETA3, 3, 10, 100)
+    with pytest.raises(rm.RmatError):
+        rm.rmat_table_set_flags(t, rm.RMAT_UNDIRECTED)
+    with pytest.raises(rm.RmatError):
+        rm.rmat_table_set_scramble(t, True, 1)
+    b = rm.rmat_batch_create()
+    with pytest.raises(rm.RmatError):
+        rm.rmat_batch_add(b, t, 1, 0, 10, 8)
+    with pytest.raises(rm.RmatError):
+        rm.rmat_partition_create(t, 2, 100, 1)

@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-edges", type=int, default=1 << 27)
-    ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5", "part", "kron"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5", "part", "kron", "tablebuild"], default="c2",
                     help="c2 (default): the contract line; c1/c3/c4/c5: the other configurations, one JSON line each")
     ap.add_argument("--log2m", type=int, default=LOG2M,
                     help="c2: edges per GPU = 2^log2m (default 30; smaller only for profiling captures)")
@@ -528,6 +528,33 @@ def run_kron(args):
                       "hbm_frac": 8.0 * m / dt / 1e9 / peak, "peak_source": peak_src}), flush=True)
 
 
+def run_tablebuild(args):
+    """Variable-length table construction (G500 parameters, k = 26) on the host
+    (rmat_build_table) and on the GPU (rmat_build_table_gpu, identical
+    tables), wall time per table for several bounds."""
+    import torch
+    import paper_1905_03525_gb300 as rm
+    torch.cuda.synchronize()
+    rows = []
+    for bound in (1 << 12, 1 << 16, 1 << 20, 1 << 22):
+        reps = 5 if bound <= 1 << 16 else 2
+        rm.rmat_build_table_gpu(*G500, K, bound)  # warm
+        times = {}
+        for name, fn in (("host", lambda: rm.rmat_build_table(*G500, K, bound)),
+                         ("gpu", lambda: rm.rmat_build_table_gpu(*G500, K, bound))):
+            ts = []
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                fn().free()
+                ts.append(time.perf_counter() - t0)
+            times[name] = statistics.median(ts)
+        rows.append({"bound": bound, "host_ms": times["host"] * 1e3, "gpu_ms": times["gpu"] * 1e3,
+                     "speedup": times["host"] / times["gpu"]})
+    print(json.dumps({"workload": "tablebuild", "config": {"workload": "variable-length table, G500 parameters, "
+                      "k=26; wall time of one build call including copies back to the host"},
+                      "metric": "ms per table", "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -542,6 +569,8 @@ def main():
         run_part(args)
     elif args.workload == "kron":
         run_kron(args)
+    elif args.workload == "tablebuild":
+        run_tablebuild(args)
     elif args.workload == "c5":
         from paper_1905_03525_gb300 import serve
         serve.bench(args)

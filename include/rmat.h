@@ -135,6 +135,21 @@ rmat_status rmat_table_group_info(const rmat_table *t, int group, int *entries, 
                                   int *max_len);
 
 /*
+ * rmat_build_table_gpu -- the table of rmat_build_table(a, b, c, d, k,
+ * table_bound), built on the current GPU (Sec. 3, parallelization: expand
+ * every path above a probability threshold level by level, then build the
+ * alias table).  The result is identical to rmat_build_table's -- entries,
+ * order, probabilities, weights, alias pairs and device image -- and its
+ * device copy on this GPU is the image the build produced.  One launch of a
+ * single 1024-thread CTA on `stream`; the call returns when the table is
+ * ready (synchronous).  Needs a, b, c, d >= 1e-9 (else RMAT_ERR_UNSUPPORTED; use
+ * rmat_build_table); device scratch about 30 bytes per expanded node (~4x
+ * the bound) plus the table, allocated and freed by the call.
+ */
+rmat_status rmat_build_table_gpu(double a, double b, double c, double d, int k,
+                                 uint64_t table_bound, rmat_stream_t stream, rmat_table **out);
+
+/*
  * Stochastic Kronecker graphs (Sec. 3: an n0 x n0 matrix instead of the 2 x 2
  * one in the recursion).  theta: n0 x n0 initiator, row-major, entries >= 0
  * summing to 1 (within 1e-9; divided by their sum); 2 <= n0 <= 16.  The

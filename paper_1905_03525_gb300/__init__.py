@@ -23,7 +23,7 @@ __all__ = [
     "rmat_batch_add", "rmat_batch_prepare", "rmat_batch_launch", "rmat_batch_size", "rmat_batch_free",
     "rmat_generate_batch_noalloc", "rmat_batch_add_tile", "Partition", "rmat_partition_create",
     "rmat_partition_info", "rmat_partition_tiles", "rmat_generate_partition", "rmat_free_partition",
-    "rmat_build_table_kron", "rmat_build_table_kron_fixed", "empty_edges_for",
+    "rmat_build_table_kron", "rmat_build_table_kron_fixed", "empty_edges_for", "rmat_build_table_gpu",
 ]
 
 
@@ -86,6 +86,12 @@ def _new_table(call) -> Table:
 def rmat_build_table(a, b, c, d, k, table_bound) -> Table:
     """Variable-length table of similar-probability paths (Sec. 2)."""
     return _new_table(lambda out: lib().rmat_build_table(a, b, c, d, k, table_bound, out))
+
+
+def rmat_build_table_gpu(a, b, c, d, k, table_bound, stream=None) -> Table:
+    """rmat_build_table's table, built on the current GPU (Sec. 3 parallel
+    construction); identical result."""
+    return _new_table(lambda out: lib().rmat_build_table_gpu(a, b, c, d, k, table_bound, _stream(stream), out))
 
 
 def rmat_build_table_fixed(a, b, c, d, k, ell) -> Table:

@@ -79,6 +79,7 @@ SIGNATURES = [
     ("rmat_build_table_levels", _st, [_vp, _i32, _i32, _u32, _vp]),
     ("rmat_table_set_flags", _st, [_vp, _u32]),
     ("rmat_table_set_scramble", _st, [_vp, _i32, _u64]),
+    ("rmat_build_table_gpu", _st, [_dbl, _dbl, _dbl, _dbl, _i32, _u64, _vp, _vp]),
     ("rmat_build_table_kron", _st, [_vp, _i32, _i32, _u64, _vp]),
     ("rmat_build_table_kron_fixed", _st, [_vp, _i32, _i32, _i32, _vp]),
     ("rmat_batch_add_tile", _st, [_vp, _vp, _u64, _u64, _u64, _i32, _u64, _u64, _vp]),

@@ -279,3 +279,13 @@ def test_kron_host_checks():
         rm.rmat_batch_add(b, t, 1, 0, 10, 8)
     with pytest.raises(rm.RmatError):
         rm.rmat_partition_create(t, 2, 100, 1)
+
+
+def test_gpu_table_build_fails_cleanly_without_a_device():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    with pytest.raises(rm.RmatError):
+        rm.rmat_build_table_gpu(0.57, 0.19, 0.19, 0.05, 26, 4096)
+    with pytest.raises(rm.RmatError):
+        rm.rmat_build_table_gpu(0.57, 0.19, 0.19, 0.05, 26, 4)   # bound below 5

@@ -38,7 +38,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic of one full-size k_alias launch of this workload (2^30 edges), from
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (1 pass) on the bench
 # command; valid only for the kernel sources whose hash is recorded with it.
-TRAFFIC = {"kernel_sha256_16": "0a9df50ab62e0c33", "bytes_per_launch": 0.87e6 + 8.53e9}
+TRAFFIC = {"kernel_sha256_16": "6c12cfcee630e219", "bytes_per_launch": 0.08e6 + 8.53e9}
 KERNEL_SOURCES = ("paper_1905_03525_gb300/csrc/rmat_device.cuh", "paper_1905_03525_gb300/csrc/rmat_kernels.cu")
 
 

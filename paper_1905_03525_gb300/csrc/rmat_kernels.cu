@@ -144,8 +144,7 @@ __device__ __forceinline__ void put_final(uint32_t stage, uint32_t idx, const ty
 }
 
 // Phase 1 over a tile: one Philox block and up to `draws1` draws per edge,
-// two edges per lane in flight (edges it*32 + lane and (it+1)*32 + lane) so
-// that their independent Philox chains and table loads overlap.  Finished
+// several edges per lane in flight.  Finished
 // edges go to their output slot; unfinished ones leave their raw accumulators
 // in the same slot, their level count in p_fill, and a bit in the lane's mask
 // (bit i = edge i*32 + lane).
@@ -181,36 +180,43 @@ __device__ __forceinline__ uint32_t phase1(const Job &J, const uint32_t (&ks)[20
         dev::sts8(p_fill + idx, acc.filled);
         pm |= uint32_t(!done) << it;
     };
-    for (uint32_t it = 0; it < iters; it += 2) {
-        const uint32_t idx0 = it * 32 + lane;
-        const uint4 w0 = edge_block<KS>(J, ks, 0u, ebase + idx0);
-        const uint4 w1 = edge_block<KS>(J, ks, 0u, ebase + idx0 + 32);
-        Acc a0, a1;
-        a0.clear();
-        a1.clear();
-        if constexpr (PRE) {
-            // batched jobs may start below the top level (a partition tile)
-            using Word = typename AccT<U64>::word;
-            a0.row = a1.row = Word(J.pre_row);
-            a0.col = a1.col = Word(J.pre_col);
-            a0.filled = a1.filled = J.pre_len;
+    // E edges per lane in flight (edges it*32 + lane, (it+1)*32 + lane, ...):
+    // their independent Philox chains and table loads overlap.  Four pays off
+    // for compact entries, u32 IDs and the plain epilogue; elsewhere the extra
+    // registers would spill.
+    constexpr int E = (FMT == 0 && !U64 && !(EPI & (kEpiScr | kEpiScrFlag))) ? 4 : 2;
+    for (uint32_t it = 0; it < iters; it += E) {
+        uint4 w[E];
+        Acc a[E];
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            w[q] = edge_block<KS>(J, ks, 0u, ebase + (it + q) * 32 + lane);
+            a[q].clear();
+            if constexpr (PRE) {
+                // batched jobs may start below the top level (a partition tile)
+                using Word = typename AccT<U64>::word;
+                a[q].row = Word(J.pre_row);
+                a[q].col = Word(J.pre_col);
+                a[q].filled = J.pre_len;
+            }
         }
-        step(a0, w0.x);
-        step(a1, w1.x);
+#pragma unroll
+        for (int q = 0; q < E; ++q) step(a[q], w[q].x);
         if (J.draws1 > 1) {
-            step(a0, w0.y);
-            step(a1, w1.y);
+#pragma unroll
+            for (int q = 0; q < E; ++q) step(a[q], w[q].y);
         }
         if (J.draws1 > 2) {
-            step(a0, w0.z);
-            step(a1, w1.z);
+#pragma unroll
+            for (int q = 0; q < E; ++q) step(a[q], w[q].z);
         }
         if (J.draws1 > 3) {
-            step(a0, w0.w);
-            step(a1, w1.w);
+#pragma unroll
+            for (int q = 0; q < E; ++q) step(a[q], w[q].w);
         }
-        settle(a0, it);
-        if (it + 1 < iters) settle(a1, it + 1);  // tiles may hold an odd number of 32-edge rows
+#pragma unroll
+        for (int q = 0; q < E; ++q)
+            if (q == 0 || it + q < iters) settle(a[q], it + q);  // a tile may end inside the group
     }
     return pm;
 }

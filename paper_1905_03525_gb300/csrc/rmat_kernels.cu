@@ -798,12 +798,11 @@ rmat_status launch_kron(const rmat_table *t, const uint32_t *dblob, const AliasP
         J.pw[j] = j <= t->k ? v : 0;  // n0^k may be 2^64 (wraps to 0; used only times 0)
         v *= uint64_t(t->n0);
     }
-    unsigned __int128 D = 1;
+    const uint64_t two32 = uint64_t(1) << 32;
+    uint64_t D = 1;  // n0^d while it is <= 2^32, then held above 2^32 (no wrap-around)
     for (int d = 0; d <= 32; ++d) {
-        J.mg[d] = (d >= 1 && D <= (unsigned __int128)(uint64_t(1) << 32))
-                      ? uint64_t(((unsigned __int128)1 << 64) / D) + 1
-                      : 0;
-        D *= uint64_t(t->n0);
+        J.mg[d] = (d >= 1 && D <= two32) ? uint64_t(((unsigned __int128)1 << 64) / D) + 1 : 0;
+        D = D <= two32 ? D * uint64_t(t->n0) : D;
     }
     const uint64_t blocks = (count + plan.threads - 1) / plan.threads;
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(blocks, uint64_t(plan.sms) * plan.ctas_per_sm)));

@@ -134,8 +134,11 @@ double now_s(const rmat_server *s) {
 }
 
 constexpr int kThreads = 1024;
+// The smallest warp tile a step uses (the automatic table bound keeps every
+// table stageable beside tiles of this size), and the unit size it implies
+// (units hold 16 tiles per warp, so larger tiles only make fewer units).
 int tile_for(bool u64) { return u64 ? 128 : 256; }
-uint64_t unit_edges_for(bool u64) { return uint64_t(kThreads / 32) * tile_for(u64) * 4; }
+uint64_t unit_edges_for(bool u64) { return uint64_t(kThreads / 32) * tile_for(u64) * 16; }
 
 void release(rmat_server *s, Request *r) {
     if (r->blob_bytes) s->arena->release(r->blob_off, r->blob_bytes);
@@ -202,8 +205,15 @@ rmat_status wait_stream(rmat_server *s) {
 rmat_status run_step(rmat_server *s, const std::vector<Request *> &picked, const std::vector<uint64_t> &counts,
                      bool u64) {
     if (picked.empty()) return RMAT_OK;
-    const uint64_t ue = unit_edges_for(u64);
-    const int tile = tile_for(u64);
+    // 512-edge tiles (256 for u64) unless the step's largest table would not
+    // fit in shared memory beside them (as rmat_batch_prepare's default)
+    size_t largest = 0;
+    for (const Request *r : picked) largest = std::max(largest, r->blob_bytes);
+    int tile = u64 ? 256 : 512;
+    while (tile > tile_for(u64) &&
+           16 + size_t(kThreads / 32) * warp_bytes(u64, false, tile) + largest > size_t(s->props.max_smem))
+        tile /= 2;
+    const uint64_t ue = uint64_t(kThreads / 32) * tile * 16;
     const size_t per_warp = warp_bytes(u64, false, tile);
     const size_t budget = size_t(s->props.max_smem) - 16 - size_t(kThreads / 32) * per_warp;
     uint64_t units = 0;

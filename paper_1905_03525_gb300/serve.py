@@ -151,9 +151,17 @@ def bench(args) -> None:
         trace2 = served_trace(args.requests, rate=sustain, seed=2001)
         s2 = summarise(run_trace(srv, trace2))
         st = srv.stats()
+    # the same offered trace with one request on the GPU at a time (FIFO, one
+    # graph per launch, same chunks and consumer): what continuous batching
+    # is measured against
+    with Server(budget, chunk_edges=1 << 28, step_edges=1 << 31, max_active=1) as fifo:
+        fifo.wait(fifo.submit(0.57, 0.19, 0.19, 0.05, 16, 1 << 20, 1))
+        s3 = summarise(run_trace(fifo, trace))
     line = {"workload": "c5", "config": {"workload": "served: Poisson arrivals, k~U{12..30}, ef in {4,8,16,32}, "
                                           "m=ef*2^k, (a,b,c,d)~Dirichlet(57,19,19,5), 2^28-edge chunks",
                                           "hbm_budget_bytes": budget, "max_active": 64, "step_edges": 1 << 31},
             "metric": "edges/s", "value": s1["edges_per_s"], "offered": {"rate_per_s": args.rate, **s1},
-            "sustainable": {"rate_per_s": sustain, **s2}, "server_steps": st["steps"]}
+            "sustainable": {"rate_per_s": sustain, **s2},
+            "fifo_one_request_at_a_time": {"rate_per_s": args.rate, **s3},
+            "speedup_vs_fifo": s1["edges_per_s"] / s3["edges_per_s"], "server_steps": st["steps"]}
     print(json.dumps(line), flush=True)

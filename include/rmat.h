@@ -368,7 +368,7 @@ typedef struct {
     int k;
     uint64_t m;           /* edges 0..m-1 of the graph, m >= 1 */
     uint64_t seed;
-    uint64_t table_bound; /* variable-length table bound; 0 = the largest power of two <= 4096
+    uint64_t table_bound; /* variable-length table bound; 0 = the largest power of two <= 8192
                              whose table the batched kernel can keep in shared memory */
     unsigned flags;       /* RMAT_UNDIRECTED or 0 */
     int scramble;         /* nonzero: relabel vertices as rmat_table_set_scramble(t, 1, scramble_seed) */

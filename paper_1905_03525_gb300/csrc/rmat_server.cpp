@@ -441,13 +441,13 @@ rmat_status rmat_server_submit(rmat_server *s, const rmat_request_t *req, uint64
     clear_error();
     if (!s || !req) return fail(RMAT_ERR_INVALID_ARGUMENT, "NULL argument");
     if (req->m == 0) return fail(RMAT_ERR_INVALID_ARGUMENT, "a request needs m >= 1 edges");
-    // table_bound 0: the largest power-of-two bound <= 4096 whose blob the
+    // table_bound 0: the largest power-of-two bound <= 8192 whose blob the
     // batched kernel can stage in shared memory (deep paths of skewed
     // parameters make wide, 36-byte columns); otherwise exactly the bound asked.
     const bool u64 = req->k > 32;
     const size_t smem_budget = size_t(s->props.max_smem) - 16 -
                                size_t(kThreads / 32) * warp_bytes(u64, false, tile_for(u64));
-    uint64_t bound = req->table_bound ? req->table_bound : 4096;
+    uint64_t bound = req->table_bound ? req->table_bound : 8192;
     rmat_table *t = nullptr;
     for (;;) {
         if (rmat_status st = rmat_build_table(req->a, req->b, req->c, req->d, req->k, bound, &t)) return st;

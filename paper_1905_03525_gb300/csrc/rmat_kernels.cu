@@ -595,7 +595,7 @@ __global__ void __launch_bounds__(256) k_checksum(BatchArgs B, unsigned long lon
         const uint64_t f0 = (unit - J.unit_begin) * B.unit_edges;
         const uint64_t end = min(J.count, f0 + B.unit_edges);
         unsigned long long acc = 0;
-        for (uint64_t i = f0 + threadIdx.x; i < end; i += blockDim.x) {
+        auto edge = [&](uint64_t i) {
             uint64_t r, c;
             if (U64) {
                 const ulonglong2 v = reinterpret_cast<const ulonglong2 *>(J.out)[i];
@@ -606,11 +606,22 @@ __global__ void __launch_bounds__(256) k_checksum(BatchArgs B, unsigned long lon
                 r = v.x;
                 c = v.y;
             }
-            uint64_t x = (J.e0 + i) * 0x9E3779B97F4A7C15ull + r * 0xC2B2AE3D27D4EB4Full + c * 0x165667B19E3779F9ull;
+            return make_ulonglong2(r, c);
+        };
+        auto mix = [&](uint64_t i, ulonglong2 v) {
+            uint64_t x = (J.e0 + i) * 0x9E3779B97F4A7C15ull + v.x * 0xC2B2AE3D27D4EB4Full + v.y * 0x165667B19E3779F9ull;
             x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
             x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-            acc += x ^ (x >> 31);
+            return x ^ (x >> 31);
+        };
+        // four independent loads in flight per thread before the arithmetic
+        const uint64_t bd = blockDim.x;
+        uint64_t i = f0 + threadIdx.x;
+        for (; i + 3 * bd < end; i += 4 * bd) {
+            const ulonglong2 v0 = edge(i), v1 = edge(i + bd), v2 = edge(i + 2 * bd), v3 = edge(i + 3 * bd);
+            acc += mix(i, v0) + mix(i + bd, v1) + mix(i + 2 * bd, v2) + mix(i + 3 * bd, v3);
         }
+        for (; i < end; i += bd) acc += mix(i, edge(i));
         for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
         if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
         __syncthreads();

@@ -264,3 +264,14 @@ def test_scrambled_ids_match_oracle(kind, k, undirected):
     assert_same(gpu_edges(t, k, 77, 5, m), ref)
     rm.rmat_table_set_scramble(t, False)
     assert_same(gpu_edges(t, k, 77, 5, m), oracle.generate(ot, k, 77, 5, m, undirected=undirected))
+
+
+@pytest.mark.parametrize("e0,count", [((1 << 64) - 5000, 5000), ((1 << 63) + 17, 3000), ((1 << 32) - 7, 64)])
+def test_edge_offsets_at_the_top_of_the_counter(e0, count):
+    """Edge numbers near 2^64 (counter words 2 and 3 of the Philox block)."""
+    k = 26
+    t = rm.rmat_build_table(*G500, k, 4096)
+    ot = oracle.Table.variable(*G500, k, 4096)
+    assert_same(gpu_edges(t, k, 99, e0, count), oracle.generate([ot], k, 99, e0, count))
+    with pytest.raises(rm.RmatError):     # e0 + count past 2^64 is refused on the host
+        rm.rmat_generate(t, 99, (1 << 64) - 10, 11, rm.empty_edges(11, k))

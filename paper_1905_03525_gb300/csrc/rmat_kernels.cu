@@ -245,14 +245,17 @@ __device__ __forceinline__ void gen_tile(const Job &J, const uint32_t (&ks)[20],
     __syncwarp();
 
     if constexpr (LEVELS) {
-        for (uint32_t base = 0; base < n; base += 32) {
-            const uint32_t idx = base + lane;
-            const uint64_t e = ebase + idx;
-            Acc acc;
-            acc.clear();
+        // two edges per lane (idx, idx + 32) share each group's descriptor
+        for (uint32_t base = 0; base < n; base += 64) {
+            const uint32_t idx0 = base + lane, idx1 = idx0 + 32;
+            Acc a0, a1;
+            a0.clear();
+            a1.clear();
             for (int q = 0; 4 * q < J.ngroups; ++q) {
-                const uint4 w = edge_block<KS>(J, ks, uint32_t(q), e);
-                const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+                const uint4 w0 = edge_block<KS>(J, ks, uint32_t(q), ebase + idx0);
+                const uint4 w1 = edge_block<KS>(J, ks, uint32_t(q), ebase + idx1);
+                const uint32_t ws0[4] = {w0.x, w0.y, w0.z, w0.w};
+                const uint32_t ws1[4] = {w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int g = 4 * q + i;
@@ -267,11 +270,13 @@ __device__ __forceinline__ void gen_tile(const Job &J, const uint32_t (&ks)[20],
                         } else {
                             Gg = dev::group<SMEM>(sblob, gblob, uint32_t(g));
                         }
-                        dev::draw<FMT, SMEM>(Gg, ws[i], acc);
+                        dev::draw<FMT, SMEM>(Gg, ws0[i], a0);
+                        dev::draw<FMT, SMEM>(Gg, ws1[i], a1);
                     }
                 }
             }
-            if (idx < n) put_final<U64, EPI>(stage, idx, acc, J, S);
+            if (idx0 < n) put_final<U64, EPI>(stage, idx0, a0, J, S);
+            if (idx1 < n) put_final<U64, EPI>(stage, idx1, a1, J, S);
         }
     } else {
         const uint32_t pm = n == uint32_t(W.tile)

@@ -266,9 +266,10 @@ def test_scrambled_ids_match_oracle(kind, k, undirected):
     assert_same(gpu_edges(t, k, 77, 5, m), oracle.generate(ot, k, 77, 5, m, undirected=undirected))
 
 
-@pytest.mark.parametrize("e0,count", [((1 << 64) - 5000, 5000), ((1 << 63) + 17, 3000), ((1 << 32) - 7, 64)])
+@pytest.mark.parametrize("e0,count", [((1 << 64) - 5001, 5000), ((1 << 63) + 17, 3000), ((1 << 32) - 7, 64)])
 def test_edge_offsets_at_the_top_of_the_counter(e0, count):
-    """Edge numbers near 2^64 (counter words 2 and 3 of the Philox block)."""
+    """Edge numbers near 2^64 (counter words 2 and 3 of the Philox block);
+    edge_offset + count must fit 64 bits, so the last usable edge is 2^64 - 2."""
     k = 26
     t = rm.rmat_build_table(*G500, k, 4096)
     ot = oracle.Table.variable(*G500, k, 4096)

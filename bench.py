@@ -39,16 +39,38 @@ FALLBACK_HBM_GBS = 6800.0
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (1 pass) on the bench
 # command; valid only for the kernel sources whose hash is recorded with it.
 TRAFFIC = {"kernel_sha256_16": "6c12cfcee630e219", "bytes_per_launch": 0.08e6 + 8.53e9}
+# Warp instructions per edge of the same kernel (smsp__inst_executed.sum / 2^26 on
+# the m=2^26 `ncu --set full` capture of this workload), valid for the same hash.
+INSTR = {"kernel_sha256_16": "0000000000000000", "warp_instr_per_edge": None}
 KERNEL_SOURCES = ("paper_1905_03525_gb300/csrc/rmat_device.cuh", "paper_1905_03525_gb300/csrc/rmat_kernels.cu")
 
 
-def measured_traffic(log2m: int):
+def kernel_hash() -> str:
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
-    if h.hexdigest()[:16] != TRAFFIC["kernel_sha256_16"] or log2m != LOG2M:
+    return h.hexdigest()[:16]
+
+
+def issue_roofline(edges_per_s: float, sm_mhz: float):
+    """The kernel's integer-issue ceiling: achieved warp instructions per
+    second against SMs x 4 schedulers x the SM clock sampled in the run."""
+    import torch
+    if INSTR["kernel_sha256_16"] != kernel_hash() or not INSTR["warp_instr_per_edge"] or not sm_mhz:
+        return None
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    achieved = edges_per_s * INSTR["warp_instr_per_edge"]
+    peak = sms * 4 * sm_mhz * 1e6
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "warp-instr/s", "frac": achieved / peak,
+            "warp_instr_per_edge": INSTR["warp_instr_per_edge"],
+            "source": "smsp__inst_executed.sum of the m=2^26 ncu capture of the same kernel sources; "
+                      "peak = SMs x 4 schedulers x median SM clock of this run"}
+
+
+def measured_traffic(log2m: int):
+    if kernel_hash() != TRAFFIC["kernel_sha256_16"] or log2m != LOG2M:
         return None  # kernel changed since the counters were taken
     return TRAFFIC["bytes_per_launch"]
 
@@ -311,6 +333,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": measured_traffic(args.log2m), "peak_source": f"{peak_src} hbm_gbs (copy)",
                      "algorithmic_bytes_per_launch": 8 * m, "avg_launch_ms": avg_launch_s * 1e3},
+        "issue_roofline": issue_roofline(m / avg_launch_s, cs["sm_mhz"]),
         "cpu_baseline": cb,
         "comparators": {"naive_per_bit_gpu": {"value": world * m / naive_s, "unit": "edges/s",
                                               "note": "k Philox words and quadrant draws per edge, same GPU"},

@@ -168,8 +168,10 @@ def build_tuned_table(k: int, abcd, m: int | None = None, choice=None):
     return rmat_build_table(*abcd, k, bound)
 
 
-def batch_blob_budget(threads: int = 1024, tile: int = 256, u64: bool = False) -> int:
-    """Shared memory the batched kernel has left for a staged table blob."""
+def batch_blob_budget(threads: int = 1024, tile: int = 512, u64: bool = False) -> int:
+    """Shared memory the batched kernel has left for a staged table blob beside
+    its default 512-edge tiles (a larger table would make a whole wave fall
+    back to 256-edge tiles)."""
     import torch
     smem = torch.cuda.get_device_properties(torch.cuda.current_device()).shared_memory_per_block_optin
     per_warp = tile * (16 if u64 else 8) + 3 * tile

@@ -174,7 +174,7 @@ rmat_status prepare_side(rmat_batch *b, bool u64, const DeviceProps &props, Side
     s.args.max_blob_bytes = max_blob;
     s.args.tile = tile;
     s.args.err = props.err;
-    for (const Job &J : jobs) s.args.prefixed |= J.pre_len ? 1 : 0;
+    for (const Job &J : jobs) s.args.general |= (J.pre_len || (J.flags & kScrambleFlag)) ? 1 : 0;
     return RMAT_OK;
 }
 

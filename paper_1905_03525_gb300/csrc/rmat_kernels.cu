@@ -182,9 +182,10 @@ __device__ __forceinline__ uint32_t phase1(const Job &J, const uint32_t (&ks)[20
     };
     // E edges per lane in flight (edges it*32 + lane, (it+1)*32 + lane, ...):
     // their independent Philox chains and table loads overlap.  Four pays off
-    // for compact entries, u32 IDs and the plain epilogue; elsewhere the extra
-    // registers would spill.
-    constexpr int E = (FMT == 0 && !U64 && !(EPI & (kEpiScr | kEpiScrFlag))) ? 4 : 2;
+    // in the single-graph kernel for compact entries, u32 IDs and the plain
+    // epilogue; elsewhere two (more would spill, or measured slower in the
+    // batched kernel).
+    constexpr int E = (KS && FMT == 0 && !U64 && !(EPI & (kEpiScr | kEpiScrFlag))) ? 4 : 2;
     for (uint32_t it = 0; it < iters; it += E) {
         uint4 w[E];
         Acc a[E];
@@ -245,17 +246,24 @@ __device__ __forceinline__ void gen_tile(const Job &J, const uint32_t (&ks)[20],
     __syncwarp();
 
     if constexpr (LEVELS) {
-        // two edges per lane (idx, idx + 32) share each group's descriptor
-        for (uint32_t base = 0; base < n; base += 64) {
-            const uint32_t idx0 = base + lane, idx1 = idx0 + 32;
-            Acc a0, a1;
-            a0.clear();
-            a1.clear();
+        // EL edges per lane (idx, idx + 32, ...) share each group's descriptor;
+        // two in the single-graph kernel, one in the batched kernel, whose
+        // register copy of the job leaves no room for a second.
+        constexpr int EL = KS ? 2 : 1;
+        for (uint32_t base = 0; base < n; base += 32 * EL) {
+            Acc a[EL];
+#pragma unroll
+            for (int q = 0; q < EL; ++q) a[q].clear();
             for (int q = 0; 4 * q < J.ngroups; ++q) {
-                const uint4 w0 = edge_block<KS>(J, ks, uint32_t(q), ebase + idx0);
-                const uint4 w1 = edge_block<KS>(J, ks, uint32_t(q), ebase + idx1);
-                const uint32_t ws0[4] = {w0.x, w0.y, w0.z, w0.w};
-                const uint32_t ws1[4] = {w1.x, w1.y, w1.z, w1.w};
+                uint32_t ws[EL][4];
+#pragma unroll
+                for (int x = 0; x < EL; ++x) {
+                    const uint4 w = edge_block<KS>(J, ks, uint32_t(q), ebase + base + 32 * x + lane);
+                    ws[x][0] = w.x;
+                    ws[x][1] = w.y;
+                    ws[x][2] = w.z;
+                    ws[x][3] = w.w;
+                }
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int g = 4 * q + i;
@@ -270,13 +278,16 @@ __device__ __forceinline__ void gen_tile(const Job &J, const uint32_t (&ks)[20],
                         } else {
                             Gg = dev::group<SMEM>(sblob, gblob, uint32_t(g));
                         }
-                        dev::draw<FMT, SMEM>(Gg, ws0[i], a0);
-                        dev::draw<FMT, SMEM>(Gg, ws1[i], a1);
+#pragma unroll
+                        for (int x = 0; x < EL; ++x) dev::draw<FMT, SMEM>(Gg, ws[x][i], a[x]);
                     }
                 }
             }
-            if (idx0 < n) put_final<U64, EPI>(stage, idx0, a0, J, S);
-            if (idx1 < n) put_final<U64, EPI>(stage, idx1, a1, J, S);
+#pragma unroll
+            for (int x = 0; x < EL; ++x) {
+                const uint32_t idx = base + 32 * x + lane;
+                if (idx < n) put_final<U64, EPI>(stage, idx, a[x], J, S);
+            }
         }
     } else {
         const uint32_t pm = n == uint32_t(W.tile)
@@ -446,9 +457,10 @@ __device__ __forceinline__ void batch_unit(const Job &J, const Scramble &S, uint
     }
 }
 
-// PRE: some job starts below the top level (a partition tile); the variant
-// without it keeps the job's prefix out of the registers.
-template <bool U64, bool PRE>
+// GEN: some job starts below the top level (a partition tile) or relabels its
+// IDs; the plain variant keeps the prefix and the relabelling test out of the
+// registers, which lets compact u32 tables run four edges per lane.
+template <bool U64, bool GEN>
 __global__ void __launch_bounds__(1024) k_batch(BatchArgs B) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
@@ -500,7 +512,8 @@ __global__ void __launch_bounds__(1024) k_batch(BatchArgs B) {
         const int sel = (J.fmt ? 8 : 0) | (J.smem ? 4 : 0) | (J.levels ? 2 : 0) | ((J.flags & RMAT_UNDIRECTED) ? 1 : 0);
         const Scramble &S = B.scr[jid];  // read (from global memory) only when relabelling
 #define RMAT_UNIT(F, SM, L, U) \
-    batch_unit<U64, F, SM, L, (U ? kEpiUndir : 0) | kEpiScrFlag, PRE>(J, S, sblob, local, B.unit_edges, nwarps, warp, W)
+    batch_unit<U64, F, SM, L, (U ? kEpiUndir : 0) | (GEN ? kEpiScrFlag : 0), GEN>(J, S, sblob, local, B.unit_edges, \
+                                                                                 nwarps, warp, W)
         switch (sel) {
             case 0: RMAT_UNIT(0, false, false, false); break;
             case 1: RMAT_UNIT(0, false, false, true); break;
@@ -965,10 +978,10 @@ size_t batch_smem_bytes(bool u64, int threads, int tile, uint32_t max_blob_bytes
     return 16 + size_t(max_blob_bytes) + size_t(threads / 32) * warp_region_bytes(u64, false, tile);
 }
 
-void *batch_kernel(bool u64, bool prefixed) {
-    if (u64) return prefixed ? reinterpret_cast<void *>(&k_batch<true, true>)
-                             : reinterpret_cast<void *>(&k_batch<true, false>);
-    return prefixed ? reinterpret_cast<void *>(&k_batch<false, true>) : reinterpret_cast<void *>(&k_batch<false, false>);
+void *batch_kernel(bool u64, bool general) {
+    if (u64) return general ? reinterpret_cast<void *>(&k_batch<true, true>)
+                            : reinterpret_cast<void *>(&k_batch<true, false>);
+    return general ? reinterpret_cast<void *>(&k_batch<false, true>) : reinterpret_cast<void *>(&k_batch<false, false>);
 }
 
 rmat_status batch_occupancy(bool u64, int threads, size_t smem, int &per_sm) {
@@ -988,7 +1001,7 @@ rmat_status batch_occupancy(bool u64, int threads, size_t smem, int &per_sm) {
 }
 
 rmat_status launch_batch(bool u64, const BatchArgs &args, int grid, int threads, size_t smem, cudaStream_t stream) {
-    void *fn = batch_kernel(u64, args.prefixed != 0);
+    void *fn = batch_kernel(u64, args.general != 0);
     cudaError_t e = cudaMemsetAsync(args.counter, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     BatchArgs a = args;

@@ -64,7 +64,7 @@ struct BatchArgs {
     uint32_t max_blob_bytes;   // shared bytes reserved for a staged blob
     int tile;
     unsigned *err;
-    int prefixed;              // some job is a partition tile (pre_len > 0)
+    int general;               // some job is a partition tile (pre_len > 0) or relabels IDs
 };
 
 // One launch of the Kronecker kernel (n0 > 2): edges e0 .. e0+count-1.

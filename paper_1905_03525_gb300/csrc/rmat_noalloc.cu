@@ -169,6 +169,7 @@ extern "C" rmat_status rmat_generate_batch_noalloc(const rmat_table *const *tabl
     args.max_blob_bytes = max_blob;
     args.tile = tile;
     args.err = props.err;
+    for (uint32_t i = 0; i < n; ++i) args.general |= tables[i]->scramble ? 1 : 0;
     const int grid = int(std::min<uint64_t>(uint64_t(props.sms) * per_sm, units));
     return launch_batch(u64, args, grid, threads, smem, stream);
 }

@@ -248,6 +248,7 @@ rmat_status run_step(rmat_server *s, const std::vector<Request *> &picked, const
     a.max_blob_bytes = max_blob;
     a.tile = tile;
     a.err = s->props.err;
+    for (const Request *r : picked) a.general |= r->table->scramble ? 1 : 0;
     const size_t smem = batch_smem_bytes(u64, kThreads, tile, max_blob);
     int per_sm = 0;
     if (rmat_status st = batch_occupancy(u64, kThreads, smem, per_sm)) return st;

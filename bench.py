@@ -518,12 +518,28 @@ def run_part(args):
         plain_s = _events_time(lambda: rm.rmat_generate(table, SEED, 0, m, out, s), s, args.steps)
     rm.rmat_check_device_errors()
     peak, peak_src = measured_peak()
+    # the oracle beside it (one core): its own split, then edges of the first tiles
+    import oracle
+    t0 = time.perf_counter()
+    tiles = oracle.partition(G500, t, m, SEED)
+    ot = oracle.Table.variable(*G500, k, BOUND)
+    done, sample = 0, 1 << 20
+    for R, C, n, f in zip(tiles["row"], tiles["col"], tiles["count"], tiles["first"]):
+        take = int(min(n, sample - done))
+        oracle.generate_tile(ot, k, t, int(R), int(C), SEED, int(f), take)
+        done += take
+        if done >= sample:
+            break
+    cpu_s = time.perf_counter() - t0
     print(json.dumps({"workload": "part", "config": {"workload": f"R-MAT k={k}, m=2^{args.log2m}, G500 parameters, "
                       f"table bound {BOUND}, {1 << t}x{1 << t} tiles, one PE (all tile rows), u32", "tile_levels": t},
                       "metric": "edges/s", "edges": edges, "tiles": ntiles, "host_plan_ms": plan_s * 1e3,
                       "partitioned_edges_per_s": edges / part_s, "ms_per_launch": part_s * 1e3,
                       "hbm_frac": 8.0 * edges / part_s / 1e9 / peak, "peak_source": peak_src,
-                      "plain_single_launch_edges_per_s": m / plain_s}), flush=True)
+                      "plain_single_launch_edges_per_s": m / plain_s,
+                      "cpu_baseline": {"value": done / cpu_s, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                                       "sample": f"the oracle's tile split of the whole graph, then the first {done} "
+                                                 "edges in tile order, one thread"}}), flush=True)
 
 
 def run_kron(args):
@@ -544,11 +560,20 @@ def run_kron(args):
     rm.rmat_check_device_errors()
     peak, peak_src = measured_peak()
     info = rm.rmat_table_info(table)
+    import oracle
+    ot = oracle.KronTable.variable(np.array(KRON3), 3, k, BOUND)
+    sample = 1 << 20
+    t0 = time.perf_counter()
+    oracle.kron_generate(ot, k, SEED, 0, sample)
+    cpu_s = time.perf_counter() - t0
     print(json.dumps({"workload": "kron", "config": {"workload": f"stochastic Kronecker graph, 3x3 initiator {KRON3}, "
                       f"k={k} (3^{k} vertices), m=2^{args.log2m}, table bound {BOUND} ({info['entries']} entries), "
                       "u32", "n0": 3, "k": k},
                       "metric": "edges/s", "value": m / dt, "ms_per_launch": dt * 1e3,
-                      "hbm_frac": 8.0 * m / dt / 1e9 / peak, "peak_source": peak_src}), flush=True)
+                      "hbm_frac": 8.0 * m / dt / 1e9 / peak, "peak_source": peak_src,
+                      "cpu_baseline": {"value": sample / cpu_s, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                                       "sample": f"edges 0..{sample - 1} of the same graph, one thread"}}),
+          flush=True)
 
 
 def run_tablebuild(args):
@@ -571,8 +596,14 @@ def run_tablebuild(args):
                 fn().free()
                 ts.append(time.perf_counter() - t0)
             times[name] = statistics.median(ts)
-        rows.append({"bound": bound, "host_ms": times["host"] * 1e3, "gpu_ms": times["gpu"] * 1e3,
-                     "speedup": times["host"] / times["gpu"]})
+        row = {"bound": bound, "host_ms": times["host"] * 1e3, "gpu_ms": times["gpu"] * 1e3,
+               "speedup": times["host"] / times["gpu"]}
+        if bound <= 1 << 20:  # the oracle beside it (plain C, one thread)
+            import oracle
+            t0 = time.perf_counter()
+            oracle.Table.variable(*G500, K, bound)
+            row["oracle_ms"] = (time.perf_counter() - t0) * 1e3
+        rows.append(row)
     print(json.dumps({"workload": "tablebuild", "config": {"workload": "variable-length table, G500 parameters, "
                       "k=26; wall time of one build call including copies back to the host"},
                       "metric": "ms per table", "rows": rows}), flush=True)

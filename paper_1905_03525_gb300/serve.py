@@ -1,5 +1,5 @@
 """Python side of the generation server: a thin wrapper over the C ABI
-(rmat_server_*) and the driver of the served workload (Poisson arrivals,
+(rmat_server_*) and the replay of the served workload (Poisson arrivals,
 latency percentiles).  All generation runs in librmat's worker thread and
 kernels; this module only submits requests and reads their status."""
 from __future__ import annotations

@@ -516,6 +516,12 @@ def run_part(args):
             rm.rmat_generate_partition(p, out, s)
         part_s = _events_time(lambda: rm.rmat_generate_partition(p, out, s), s, args.steps)
         plain_s = _events_time(lambda: rm.rmat_generate(table, SEED, 0, m, out, s), s, args.steps)
+        # local duplicate removal of the PE's edges (synchronous call)
+        rm.rmat_generate_partition(p, out, s)
+        s.synchronize()
+        t0 = time.perf_counter()
+        unique = rm.rmat_dedup_edges(out, edges, k, s)
+        dedup_s = time.perf_counter() - t0
     rm.rmat_check_device_errors()
     peak, peak_src = measured_peak()
     # the oracle beside it (one core): its own split, then edges of the first tiles
@@ -537,6 +543,8 @@ def run_part(args):
                       "partitioned_edges_per_s": edges / part_s, "ms_per_launch": part_s * 1e3,
                       "hbm_frac": 8.0 * edges / part_s / 1e9 / peak, "peak_source": peak_src,
                       "plain_single_launch_edges_per_s": m / plain_s,
+                      "dedup": {"unique_edges": unique, "ms": dedup_s * 1e3, "edges_per_s": edges / dedup_s,
+                                "note": "rmat_dedup_edges on the PE's output, wall time of the call"},
                       "cpu_baseline": {"value": done / cpu_s, "unit": "edges/s", "cores": 1, "kind": "oracle",
                                        "sample": f"the oracle's tile split of the whole graph, then the first {done} "
                                                  "edges in tile order, one thread"}}), flush=True)

@@ -337,6 +337,17 @@ rmat_status rmat_generate_partition(rmat_partition *p, void *out, rmat_stream_t 
 
 void rmat_free_partition(rmat_partition *p);
 
+/* Remove repeated edges (Sec. 3: in a partitioned graph equal edges share a
+ * tile, so each PE removes its duplicates alone).  `edges`: device array of
+ * `count` (row, col) u32 pairs of a graph with k <= 31 levels (for instance
+ * the output of rmat_generate_partition); the first occurrence of every
+ * (row, col) in array order is kept and the survivors are compacted to the
+ * front in that order; *unique receives their number.  Synchronous on
+ * `stream`; count <= 2^31; allocates and frees ~(32 x 2 + 12) bytes of
+ * device scratch per edge.  Errors: RMAT_ERR_INVALID_ARGUMENT (k, count,
+ * alignment), RMAT_ERR_OUT_OF_MEMORY, RMAT_ERR_CUDA. */
+rmat_status rmat_dedup_edges(void *edges, uint64_t count, int k, uint64_t *unique, rmat_stream_t stream);
+
 /* ---------------------------------------------------------------------- */
 /* Serving: continuous batching of generation requests                     */
 /* ---------------------------------------------------------------------- */

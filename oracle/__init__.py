@@ -324,6 +324,18 @@ def generate_partitioned(table, abcd, k, t, m, seed, row_tile_begin=0, row_tile_
     return tiles, (np.concatenate(rows), np.concatenate(cols))
 
 
+def dedup_first(row, col):
+    """Duplicate removal (Sec. 3, partitioned graphs): the first occurrence of
+    every (row, col) in array order, in that order.  IDs below 2^32."""
+    r = np.asarray(row, np.uint64)
+    c = np.asarray(col, np.uint64)
+    if len(r) and (int(r.max()) >> 32 or int(c.max()) >> 32):
+        raise ValueError("dedup_first takes IDs below 2^32")
+    _, first = np.unique((r << np.uint64(32)) | c, return_index=True)
+    keep = np.sort(first)
+    return r[keep], c[keep]
+
+
 def generate_naive(P_levels, k, seed, e0, count, undirected=False):
     P = np.ascontiguousarray(P_levels, dtype=np.float64).reshape(-1, 4)
     if P.shape[0] == 1:

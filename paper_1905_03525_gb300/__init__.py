@@ -24,6 +24,7 @@ __all__ = [
     "rmat_generate_batch_noalloc", "rmat_batch_add_tile", "Partition", "rmat_partition_create",
     "rmat_partition_info", "rmat_partition_tiles", "rmat_generate_partition", "rmat_free_partition",
     "rmat_build_table_kron", "rmat_build_table_kron_fixed", "empty_edges_for", "rmat_build_table_gpu",
+    "rmat_dedup_edges",
 ]
 
 
@@ -361,3 +362,11 @@ def rmat_generate_partition(p: Partition, out, stream=None) -> None:
 
 def rmat_free_partition(p: Partition) -> None:
     p.free()
+
+
+def rmat_dedup_edges(edges, count: int, k: int, stream=None) -> int:
+    """Remove repeated edges in place (first occurrences kept, order kept);
+    returns how many remain at the front of `edges` (Sec. 3)."""
+    n = ctypes.c_uint64()
+    check(lib().rmat_dedup_edges(_ptr(edges), count, k, ctypes.byref(n), _stream(stream)))
+    return n.value

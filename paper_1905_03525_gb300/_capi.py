@@ -88,6 +88,7 @@ SIGNATURES = [
     ("rmat_partition_tiles", _st, [_vp, _vp, _vp, _vp, _vp]),
     ("rmat_generate_partition", _st, [_vp, _vp, _vp]),
     ("rmat_free_partition", None, [_vp]),
+    ("rmat_dedup_edges", _st, [_vp, _u64, _i32, _vp, _vp]),
     ("rmat_table_info", _st, [_vp, _vp]),
     ("rmat_table_group_info", _st, [_vp, _i32, _vp, _vp, _vp]),
     ("rmat_table_export", _st, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),

@@ -289,3 +289,9 @@ def test_gpu_table_build_fails_cleanly_without_a_device():
         rm.rmat_build_table_gpu(0.57, 0.19, 0.19, 0.05, 26, 4096)
     with pytest.raises(rm.RmatError):
         rm.rmat_build_table_gpu(0.57, 0.19, 0.19, 0.05, 26, 4)   # bound below 5
+
+
+def test_dedup_host_checks():
+    with pytest.raises(rm.RmatError):
+        rm.rmat_dedup_edges(8, 10, 32)        # k above 31
+    assert rm.rmat_dedup_edges(8, 0, 20) == 0  # nothing to do, no device needed

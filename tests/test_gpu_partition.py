@@ -122,3 +122,54 @@ def test_partition_full_size_two_pes():
         del out
         torch.cuda.empty_cache()
     assert total == m
+
+
+def _dedup_gpu(out, n, k):
+    u = rm.rmat_dedup_edges(out, n, k)
+    torch.cuda.synchronize()
+    return u, pairs(out[:u], k)
+
+
+@pytest.mark.parametrize("k,m", [(8, 200_000), (12, 100_003), (3, 5000), (20, 1 << 20)])
+def test_dedup_keeps_first_occurrences(k, m):
+    t = rm.rmat_build_table(*G500, k, 256)
+    ot = oracle.Table.variable(*G500, k, 256)
+    out = rm.empty_edges(m, k)
+    rm.rmat_generate(t, 3, 0, m, out)
+    u, got = _dedup_gpu(out, m, k)
+    ref = oracle.dedup_first(*oracle.generate([ot], k, 3, 0, m))
+    assert u == len(ref[0])
+    assert_same(got, ref)
+
+
+def test_dedup_edge_cases():
+    one = rm.empty_edges(1, 10)
+    one.fill_(5)
+    assert rm.rmat_dedup_edges(one, 1, 10) == 1
+    same = rm.empty_edges(4096, 10)
+    same.fill_(7)
+    assert rm.rmat_dedup_edges(same, 4096, 10) == 1
+    assert rm.rmat_dedup_edges(same, 0, 10) == 0
+    with pytest.raises(rm.RmatError):
+        rm.rmat_dedup_edges(same, 10, 32)
+
+
+def test_partitioned_dedup_is_local():
+    """Duplicates only meet inside a tile, so the PEs' own duplicate removal
+    gives the whole graph's distinct edges, each exactly once."""
+    k, t, m, seed = 10, 2, 300_000, 4
+    table = rm.rmat_build_table(*G500, k, 512)
+    ot = oracle.Table.variable(*G500, k, 512)
+    kept = []
+    for r0, r1 in [(0, 1), (1, 4)]:
+        p = rm.rmat_partition_create(table, t, m, seed, r0, r1)
+        _, edges = rm.rmat_partition_info(p)
+        out = rm.empty_edges(edges, k)
+        rm.rmat_generate_partition(p, out)
+        u, got = _dedup_gpu(out, edges, k)
+        _, ref = oracle.generate_partitioned(ot, G500, k, t, m, seed, r0, r1)
+        assert_same(got, oracle.dedup_first(*ref))
+        kept.append(set(zip(got[0].tolist(), got[1].tolist())))
+    assert not (kept[0] & kept[1])
+    _, whole = oracle.generate_partitioned(ot, G500, k, t, m, seed)
+    assert kept[0] | kept[1] == set(zip(whole[0].tolist(), whole[1].tolist()))

@@ -670,3 +670,19 @@ def test_kron_generated_edges_follow_kronecker_power():
     cc = np.concatenate([[counts[order][small].sum()], counts[order][~small]])
     pp = np.concatenate([[probs[order][small].sum()], probs[order][~small]])
     assert _chi2_pvalue(cc, pp) > 1e-3
+
+
+@pytest.mark.parametrize("n,span", [(1, 3), (50, 4), (2000, 30), (5000, 1 << 20)])
+def test_dedup_first_is_the_first_seen_filter(n, span):
+    """Against the plain definition: walk the edges in order, keep an edge iff
+    its (row, col) was not seen before."""
+    rng = np.random.default_rng(n)
+    r = rng.integers(0, span, n).astype(np.uint64)
+    c = rng.integers(0, span, n).astype(np.uint64)
+    seen, keep = set(), []
+    for i in range(n):
+        if (int(r[i]), int(c[i])) not in seen:
+            seen.add((int(r[i]), int(c[i])))
+            keep.append(i)
+    dr, dc = oracle.dedup_first(r, c)
+    assert np.array_equal(dr, r[keep]) and np.array_equal(dc, c[keep])

@@ -472,6 +472,15 @@ rmat_status rmat_generate_batch_noalloc(const rmat_table *const *tables, const u
  * bounded wait gave up).  Synchronises the device.  RMAT_ERR_TIMEOUT if set. */
 rmat_status rmat_check_device_errors(void);
 
+/* Failure-path self-test: launches one warp that waits, through the bounded
+ * wait the generation kernels use on their table copies, on an mbarrier phase
+ * that nothing completes; after `limit` polls (1..2^22, ~0.1 us each after
+ * the first 16) it gives up and records the error in the device error word
+ * like a production kernel would, and exits.  The call synchronises the
+ * device and returns what rmat_check_device_errors then returns:
+ * RMAT_ERR_TIMEOUT, with the word cleared and the context usable. */
+rmat_status rmat_selftest_bounded_wait(uint32_t limit);
+
 /* Library version string and the compiled GPU architecture. */
 const char *rmat_version(void);
 

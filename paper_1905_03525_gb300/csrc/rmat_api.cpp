@@ -491,6 +491,15 @@ rmat_status rmat_generate_naive(const double *abcd, int k, unsigned flags, uint6
                         reinterpret_cast<cudaStream_t>(stream));
 }
 
+rmat_status rmat_selftest_bounded_wait(uint32_t limit) {
+    clear_error();
+    if (limit < 1 || limit > (1u << 22)) return fail(RMAT_ERR_INVALID_ARGUMENT, "limit must be in [1, 2^22]");
+    if (rmat_status st = launch_wait_selftest(limit, nullptr)) return st;
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("self-test: ") + cudaGetErrorString(e));
+    return rmat_check_device_errors();
+}
+
 rmat_status rmat_check_device_errors(void) {
     clear_error();
     unsigned v = 0;

@@ -83,6 +83,8 @@ struct KronJob {
 };
 
 rmat_status device_props(DeviceProps &out);
+// One warp waiting on a never-completed mbarrier phase, bounded to `limit` polls.
+rmat_status launch_wait_selftest(uint32_t limit, cudaStream_t stream);
 rmat_launch_config_t default_launch_config(const rmat_table *t);
 rmat_status plan_alias_launch(const rmat_table *t, const rmat_launch_config_t &want, AliasPlan &plan);
 Job make_job(const rmat_table *t, const uint32_t *dblob, bool smem, uint64_t seed, uint64_t e0, uint64_t count,

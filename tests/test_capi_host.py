@@ -295,3 +295,8 @@ def test_dedup_host_checks():
     with pytest.raises(rm.RmatError):
         rm.rmat_dedup_edges(8, 10, 32)        # k above 31
     assert rm.rmat_dedup_edges(8, 0, 20) == 0  # nothing to do, no device needed
+
+
+def test_selftest_argument_check():
+    with pytest.raises(rm.RmatError):
+        rm.rmat_selftest_bounded_wait(0)

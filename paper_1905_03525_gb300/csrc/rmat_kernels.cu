@@ -598,20 +598,6 @@ __global__ void __launch_bounds__(1024, 1) k_kron(const __grid_constant__ KronJo
     }
 }
 
-// Failure-path self-test: one warp waits on an mbarrier phase that nothing
-// will complete, through the same bounded wait the generation kernels use on
-// their table copies, gives up after `limit` polls and records the error in
-// the device error word, exactly as a production kernel would.
-__global__ void k_wait_selftest(unsigned *err, uint32_t limit) {
-    __shared__ __align__(8) uint64_t bar;
-    if (threadIdx.x == 0) {
-        dev::mbar_init(&bar, 1);
-        dev::fence_mbar_init();
-    }
-    __syncwarp();
-    if (threadIdx.x == 0 && !dev::mbar_wait_bounded(&bar, 0, limit)) atomicOr(err, 1u);
-}
-
 // Order-independent checksum of the edges of every job of a step: the sum
 // mod 2^64 of mix(e, row, col) over the job's edges, where
 //   x = e * 0x9E3779B97F4A7C15 + row * 0xC2B2AE3D27D4EB4F + col * 0x165667B19E3779F9
@@ -1022,15 +1008,6 @@ rmat_status launch_batch(bool u64, const BatchArgs &args, int grid, int threads,
     void *params[] = {&a};
     e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), params, smem, stream);
     if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
-    return RMAT_OK;
-}
-
-rmat_status launch_wait_selftest(uint32_t limit, cudaStream_t stream) {
-    DeviceProps props;
-    if (rmat_status st = device_props(props)) return st;
-    k_wait_selftest<<<1, 32, 0, stream>>>(props.err, limit);
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("self-test launch: ") + cudaGetErrorString(e));
     return RMAT_OK;
 }
 

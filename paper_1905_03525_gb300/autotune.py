@@ -175,7 +175,8 @@ def batch_blob_budget(threads: int = 1024, tile: int = 512, u64: bool = False) -
     import torch
     smem = torch.cuda.get_device_properties(torch.cuda.current_device()).shared_memory_per_block_optin
     per_warp = tile * (16 if u64 else 8) + 3 * tile
-    return smem - 16 - (threads // 32) * per_warp
+    header = 96  # the kernel's mbarrier, current work unit and the job's 20 Philox round keys
+    return smem - header - (threads // 32) * per_warp
 
 
 def plan_batch(graphs, representative=None, sample_edges: int = 1 << 22):

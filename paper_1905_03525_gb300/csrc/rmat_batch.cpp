@@ -94,13 +94,13 @@ rmat_status prepare_side(rmat_batch *b, bool u64, const DeviceProps &props, Side
         // shared memory beside the warps' tiles.
         tile = u64 ? 256 : 512;
         while (tile > (u64 ? 128 : 256) &&
-               16 + size_t(threads / 32) * warp_bytes(u64, false, tile) + largest_blob > size_t(props.max_smem))
+               kBatchHeaderBytes + size_t(threads / 32) * warp_bytes(u64, false, tile) + largest_blob > size_t(props.max_smem))
             tile /= 2;
     }
     const size_t per_warp = warp_bytes(u64, false, tile);
-    while (16 + size_t(threads / 32) * per_warp > size_t(props.max_smem) && threads > 128) threads /= 2;
+    while (kBatchHeaderBytes + size_t(threads / 32) * per_warp > size_t(props.max_smem) && threads > 128) threads /= 2;
     const size_t warps_bytes = size_t(threads / 32) * per_warp;
-    const size_t budget = size_t(props.max_smem) - 16 - warps_bytes;
+    const size_t budget = size_t(props.max_smem) - kBatchHeaderBytes - warps_bytes;
 
     // arena of distinct blobs
     std::map<const rmat_table *, size_t> offset;

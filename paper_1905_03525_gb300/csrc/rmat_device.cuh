@@ -117,6 +117,27 @@ __device__ __forceinline__ uint4 lds128(uint32_t addr) {
     return v;
 }
 
+// Philox4x32-10 with the round keys in shared memory at `sks` (20 words, the
+// layout of philox_ks's `ks`): one broadcast 16-byte load per two rounds.
+__device__ __forceinline__ uint4 philox_sks(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t sks) {
+#pragma unroll
+    for (int pair = 0; pair < 5; ++pair) {
+        const uint4 kk = lds128(sks + 16u * uint32_t(pair));
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint64_t m0 = uint64_t(0xD2511F53u) * c0;
+            const uint64_t m1 = uint64_t(0xCD9E8D57u) * c2;
+            const uint32_t n0 = uint32_t(m1 >> 32) ^ c1 ^ (h ? kk.z : kk.x);
+            const uint32_t n2 = uint32_t(m0 >> 32) ^ c3 ^ (h ? kk.w : kk.y);
+            c1 = uint32_t(m1);
+            c3 = uint32_t(m0);
+            c0 = n0;
+            c2 = n2;
+        }
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
 // Where one table (group) lives and how to split a word for it.
 template <bool SMEM>
 struct Group {

@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "rmat_device.cuh"
@@ -76,12 +77,26 @@ __device__ __forceinline__ dev::Group<SMEM> group0(const Job &J, uint32_t sblob)
     return G;
 }
 
-// Philox block q of edge e under the job's key.  KS: round keys read from the
-// job's precomputed schedule (kernel parameter), else derived in registers.
-template <bool KS>
-__device__ __forceinline__ uint4 edge_block(const Job &J, const uint32_t (&ks)[20], uint32_t q, uint64_t e) {
-    if constexpr (KS) return dev::philox_ks(q, 0u, uint32_t(e), uint32_t(e >> 32), ks);
-    else return dev::philox(q, 0u, uint32_t(e), uint32_t(e >> 32), J.key0, J.key1);
+// Where a tile's Philox round keys come from: the job's schedule in a kernel
+// parameter (uint32_t[20]: constant-bank operands of the xors), the schedule
+// staged in shared memory (SharedKeys: five broadcast loads per block), or
+// the job's key, advanced in registers (RegKeys).
+struct SharedKeys {
+    uint32_t addr;
+};
+struct RegKeys {};
+template <class K>
+constexpr bool kConstKeys = !std::is_same<K, SharedKeys>::value && !std::is_same<K, RegKeys>::value;
+
+// Philox block q of edge e under the job's key.
+template <class K>
+__device__ __forceinline__ uint4 edge_block(const Job &J, const K &ks, uint32_t q, uint64_t e) {
+    if constexpr (std::is_same<K, SharedKeys>::value)
+        return dev::philox_sks(q, 0u, uint32_t(e), uint32_t(e >> 32), ks.addr);
+    else if constexpr (std::is_same<K, RegKeys>::value)
+        return dev::philox(q, 0u, uint32_t(e), uint32_t(e >> 32), J.key0, J.key1);
+    else
+        return dev::philox_ks(q, 0u, uint32_t(e), uint32_t(e >> 32), ks);
 }
 
 // Write edge `idx` of the tile at shared address `stage`.
@@ -148,8 +163,8 @@ __device__ __forceinline__ void put_final(uint32_t stage, uint32_t idx, const ty
 // edges go to their output slot; unfinished ones leave their raw accumulators
 // in the same slot, their level count in p_fill, and a bit in the lane's mask
 // (bit i = edge i*32 + lane).
-template <int FMT, bool U64, bool SMEM, int EPI, bool FULL, bool KS, bool PRE>
-__device__ __forceinline__ uint32_t phase1(const Job &J, const uint32_t (&ks)[20], const Scramble &S,
+template <int FMT, bool U64, bool SMEM, int EPI, bool FULL, bool PRE, class K>
+__device__ __forceinline__ uint32_t phase1(const Job &J, const K &ks, const Scramble &S,
                                            const dev::Group<SMEM> &G0, uint64_t ebase, uint32_t n, uint32_t stage,
                                            uint32_t p_fill, int lane) {
     using Acc = typename AccT<U64>::type;
@@ -185,13 +200,13 @@ __device__ __forceinline__ uint32_t phase1(const Job &J, const uint32_t (&ks)[20
     // in the single-graph kernel for compact entries, u32 IDs and the plain
     // epilogue; elsewhere two (more would spill, or measured slower in the
     // batched kernel).
-    constexpr int E = (KS && FMT == 0 && !U64 && !(EPI & (kEpiScr | kEpiScrFlag))) ? 4 : 2;
+    constexpr int E = (kConstKeys<K> && FMT == 0 && !U64 && !(EPI & (kEpiScr | kEpiScrFlag))) ? 4 : 2;
     for (uint32_t it = 0; it < iters; it += E) {
         uint4 w[E];
         Acc a[E];
 #pragma unroll
         for (int q = 0; q < E; ++q) {
-            w[q] = edge_block<KS>(J, ks, 0u, ebase + (it + q) * 32 + lane);
+            w[q] = edge_block(J, ks, 0u, ebase + (it + q) * 32 + lane);
             a[q].clear();
             if constexpr (PRE) {
                 // batched jobs may start below the top level (a partition tile)
@@ -225,11 +240,10 @@ __device__ __forceinline__ uint32_t phase1(const Job &J, const uint32_t (&ks)[20
 // sgroups: shared address of precomputed group descriptors (uint4 {A, Bs, Ba,
 // 2^b} per group) for per-level tables staged in shared memory, or 0 to read
 // them from the blob header at every draw.
-// KS: round keys from `ks` (a kernel parameter: constant-bank operands), else
-// derived from the job's key in registers.  PRE: edges start with the job's
-// prefix levels (batched jobs).
-template <int FMT, bool U64, bool SMEM, bool LEVELS, int EPI, bool KS, bool PRE>
-__device__ __forceinline__ void gen_tile(const Job &J, const uint32_t (&ks)[20], const Scramble &S, uint32_t sblob,
+// ks: where the Philox round keys come from (see edge_block).  PRE: edges
+// start with the job's prefix levels (batched jobs).
+template <int FMT, bool U64, bool SMEM, bool LEVELS, int EPI, bool PRE, class K>
+__device__ __forceinline__ void gen_tile(const Job &J, const K &ks, const Scramble &S, uint32_t sblob,
                                          const uint32_t *gblob, const dev::Group<SMEM> &G0, uint64_t first,
                                          uint32_t n, WarpState &W, uint32_t sgroups = 0) {
     using Acc = typename AccT<U64>::type;
@@ -249,7 +263,7 @@ __device__ __forceinline__ void gen_tile(const Job &J, const uint32_t (&ks)[20],
         // EL edges per lane (idx, idx + 32, ...) share each group's descriptor;
         // two in the single-graph kernel, one in the batched kernel, whose
         // register copy of the job leaves no room for a second.
-        constexpr int EL = KS ? 2 : 1;
+        constexpr int EL = kConstKeys<K> ? 2 : 1;
         for (uint32_t base = 0; base < n; base += 32 * EL) {
             Acc a[EL];
 #pragma unroll
@@ -258,7 +272,7 @@ __device__ __forceinline__ void gen_tile(const Job &J, const uint32_t (&ks)[20],
                 uint32_t ws[EL][4];
 #pragma unroll
                 for (int x = 0; x < EL; ++x) {
-                    const uint4 w = edge_block<KS>(J, ks, uint32_t(q), ebase + base + 32 * x + lane);
+                    const uint4 w = edge_block(J, ks, uint32_t(q), ebase + base + 32 * x + lane);
                     ws[x][0] = w.x;
                     ws[x][1] = w.y;
                     ws[x][2] = w.z;
@@ -291,9 +305,8 @@ __device__ __forceinline__ void gen_tile(const Job &J, const uint32_t (&ks)[20],
         }
     } else {
         const uint32_t pm = n == uint32_t(W.tile)
-                                ? phase1<FMT, U64, SMEM, EPI, true, KS, PRE>(J, ks, S, G0, ebase, n, stage, p_fill, lane)
-                                : phase1<FMT, U64, SMEM, EPI, false, KS, PRE>(J, ks, S, G0, ebase, n, stage, p_fill,
-                                                                              lane);
+                                ? phase1<FMT, U64, SMEM, EPI, true, PRE>(J, ks, S, G0, ebase, n, stage, p_fill, lane)
+                                : phase1<FMT, U64, SMEM, EPI, false, PRE>(J, ks, S, G0, ebase, n, stage, p_fill, lane);
         // Phase 2: queue the unfinished edges of the whole tile (warp prefix
         // sum of the lanes' counts), then finish them 32 at a time.
         const uint32_t cnt = __popc(pm);
@@ -333,7 +346,7 @@ __device__ __forceinline__ void gen_tile(const Job &J, const uint32_t (&ks)[20],
                 // another draw (a warp-uniform branch)
                 for (uint32_t q = 1; q <= 17; ++q) {
                     if (!__any_sync(0xffffffffu, acc.filled < uk)) break;
-                    const uint4 w = edge_block<KS>(J, ks, q, e);
+                    const uint4 w = edge_block(J, ks, q, e);
                     if (U64) {
                         if (acc.filled < uk) dev::draw<FMT, SMEM>(G0, w.x, acc);
                     } else {
@@ -438,22 +451,23 @@ __global__ void __launch_bounds__(1024, 1) k_alias(const __grid_constant__ Job J
         const uint64_t first = t * tile;
         const uint64_t left = J.count - first;
         const uint32_t n = left < uint64_t(tile) ? uint32_t(left) : uint32_t(tile);
-        gen_tile<FMT, U64, SMEM, LEVELS, EPI, true, false>(J, J.ks, S, sblob, J.blob, G0, first, n, W, sgroups);
+        gen_tile<FMT, U64, SMEM, LEVELS, EPI, false>(J, J.ks, S, sblob, J.blob, G0, first, n, W, sgroups);
     }
     if (lane == 0 && W.issued) dev::bulk_wait_all();
 }
 
 // One work unit of a batch: edges [u * unit_edges, ...) of job unit_job[u].
 template <bool U64, int FMT, bool SMEM, bool LEVELS, int EPI, bool PRE>
-__device__ __forceinline__ void batch_unit(const Job &J, const Scramble &S, uint32_t sblob, uint64_t local_unit,
-                                           uint64_t unit_edges, int nwarps, int warp, WarpState &W) {
+__device__ __forceinline__ void batch_unit(const Job &J, const Scramble &S, SharedKeys ks, uint32_t sblob,
+                                           uint64_t local_unit, uint64_t unit_edges, int nwarps, int warp,
+                                           WarpState &W) {
     const dev::Group<SMEM> G0 = group0<SMEM>(J, sblob);
     const uint64_t f0 = local_unit * unit_edges;
     const uint64_t end = min(J.count, f0 + unit_edges);
     for (uint64_t first = f0 + uint64_t(warp) * W.tile; first < end; first += uint64_t(nwarps) * W.tile) {
         const uint64_t left = end - first;
         const uint32_t n = left < uint64_t(W.tile) ? uint32_t(left) : uint32_t(W.tile);
-        gen_tile<FMT, U64, SMEM, LEVELS, EPI, false, PRE>(J, J.ks, S, sblob, J.blob, G0, first, n, W);
+        gen_tile<FMT, U64, SMEM, LEVELS, EPI, PRE>(J, ks, S, sblob, J.blob, G0, first, n, W);
     }
 }
 
@@ -465,11 +479,13 @@ __global__ void __launch_bounds__(1024) k_batch(BatchArgs B) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
     unsigned long long *s_unit = reinterpret_cast<unsigned long long *>(smem + 8);
-    unsigned char *s_blob = smem + 16;
+    uint32_t *s_ks = reinterpret_cast<uint32_t *>(smem + 16);  // the job's Philox round keys
+    unsigned char *s_blob = smem + kBatchHeaderBytes;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const uint32_t sblob = dev::smem_u32(s_blob);
+    const SharedKeys ks{dev::smem_u32(s_ks)};
 
     if (threadIdx.x == 0) {
         dev::mbar_init(mbar, 1);
@@ -496,24 +512,30 @@ __global__ void __launch_bounds__(1024) k_batch(BatchArgs B) {
         const uint32_t jid = B.unit_job[unit];
         const Job *jp = B.jobs + jid;
         const Job J = *jp;
-        if (J.smem && jp != staged) {
-            // every warp is past the barrier above: nobody reads the old table
-            if (!stage_blob(s_blob, J.blob, J.blob_bytes, mbar, parity)) {
-                if (threadIdx.x == 0) {
-                    atomicOr(B.err, 1u);
-                    dev::mbar_wait_bounded(mbar, parity, kWaitLimit);
+        if (jp != staged) {
+            // every warp is past the barrier above: nobody reads the old job's
+            // round keys or table
+            if (threadIdx.x < 20) s_ks[threadIdx.x] = jp->ks[threadIdx.x];
+            if (J.smem) {
+                if (!stage_blob(s_blob, J.blob, J.blob_bytes, mbar, parity)) {  // (its barrier publishes s_ks)
+                    if (threadIdx.x == 0) {
+                        atomicOr(B.err, 1u);
+                        dev::mbar_wait_bounded(mbar, parity, kWaitLimit);
+                    }
+                    break;
                 }
-                break;
+                parity ^= 1u;
+            } else {
+                __syncthreads();
             }
-            parity ^= 1u;
             staged = jp;
         }
         const uint64_t local = unit - J.unit_begin;
         const int sel = (J.fmt ? 8 : 0) | (J.smem ? 4 : 0) | (J.levels ? 2 : 0) | ((J.flags & RMAT_UNDIRECTED) ? 1 : 0);
         const Scramble &S = B.scr[jid];  // read (from global memory) only when relabelling
 #define RMAT_UNIT(F, SM, L, U) \
-    batch_unit<U64, F, SM, L, (U ? kEpiUndir : 0) | (GEN ? kEpiScrFlag : 0), GEN>(J, S, sblob, local, B.unit_edges, \
-                                                                                 nwarps, warp, W)
+    batch_unit<U64, F, SM, L, (U ? kEpiUndir : 0) | (GEN ? kEpiScrFlag : 0), GEN>(J, S, ks, sblob, local, \
+                                                                                 B.unit_edges, nwarps, warp, W)
         switch (sel) {
             case 0: RMAT_UNIT(0, false, false, false); break;
             case 1: RMAT_UNIT(0, false, false, true); break;
@@ -975,7 +997,7 @@ rmat_status launch_alias(const rmat_table *t, const uint32_t *dblob, const Alias
 }
 
 size_t batch_smem_bytes(bool u64, int threads, int tile, uint32_t max_blob_bytes) {
-    return 16 + size_t(max_blob_bytes) + size_t(threads / 32) * warp_region_bytes(u64, false, tile);
+    return kBatchHeaderBytes + size_t(max_blob_bytes) + size_t(threads / 32) * warp_region_bytes(u64, false, tile);
 }
 
 void *batch_kernel(bool u64, bool general) {

@@ -54,6 +54,10 @@ struct Scramble {
 // Job flag (beside RMAT_UNDIRECTED): relabel vertex IDs with Job::scr.
 constexpr unsigned kScrambleFlag = 0x100u;
 
+// Shared memory of the batched kernel ahead of the staged table: its mbarrier
+// (8 bytes), the current work unit (8) and the job's Philox round keys (80).
+constexpr size_t kBatchHeaderBytes = 96;
+
 struct BatchArgs {
     const Job *jobs;
     const Scramble *scr;       // one per job

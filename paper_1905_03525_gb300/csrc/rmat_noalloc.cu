@@ -98,11 +98,11 @@ extern "C" rmat_status rmat_generate_batch_noalloc(const rmat_table *const *tabl
     for (uint32_t i = 0; i < n; ++i) largest_blob = std::max(largest_blob, tables[i]->image.size() * 4);
     int tile = u64 ? 256 : 512;
     while (tile > (u64 ? 128 : 256) &&
-           16 + size_t(threads / 32) * warp_bytes(u64, false, tile) + largest_blob > size_t(props.max_smem))
+           kBatchHeaderBytes + size_t(threads / 32) * warp_bytes(u64, false, tile) + largest_blob > size_t(props.max_smem))
         tile /= 2;
     const size_t per_warp = warp_bytes(u64, false, tile);
-    while (16 + size_t(threads / 32) * per_warp > size_t(props.max_smem) && threads > 128) threads /= 2;
-    const size_t budget = size_t(props.max_smem) - 16 - size_t(threads / 32) * per_warp;
+    while (kBatchHeaderBytes + size_t(threads / 32) * per_warp > size_t(props.max_smem) && threads > 128) threads /= 2;
+    const size_t budget = size_t(props.max_smem) - kBatchHeaderBytes - size_t(threads / 32) * per_warp;
     const uint64_t unit_edges = uint64_t(threads / 32) * tile * 16;  // as rmat_batch_prepare
 
     // Scratch layout: [counter][jobs][relabelling constants][unit -> job][table blobs].

@@ -211,11 +211,11 @@ rmat_status run_step(rmat_server *s, const std::vector<Request *> &picked, const
     for (const Request *r : picked) largest = std::max(largest, r->blob_bytes);
     int tile = u64 ? 256 : 512;
     while (tile > tile_for(u64) &&
-           16 + size_t(kThreads / 32) * warp_bytes(u64, false, tile) + largest > size_t(s->props.max_smem))
+           kBatchHeaderBytes + size_t(kThreads / 32) * warp_bytes(u64, false, tile) + largest > size_t(s->props.max_smem))
         tile /= 2;
     const uint64_t ue = uint64_t(kThreads / 32) * tile * 16;
     const size_t per_warp = warp_bytes(u64, false, tile);
-    const size_t budget = size_t(s->props.max_smem) - 16 - size_t(kThreads / 32) * per_warp;
+    const size_t budget = size_t(s->props.max_smem) - kBatchHeaderBytes - size_t(kThreads / 32) * per_warp;
     uint64_t units = 0;
     uint32_t max_blob = 0;
     for (size_t j = 0; j < picked.size(); ++j) {
@@ -446,7 +446,7 @@ rmat_status rmat_server_submit(rmat_server *s, const rmat_request_t *req, uint64
     // batched kernel can stage in shared memory (deep paths of skewed
     // parameters make wide, 36-byte columns); otherwise exactly the bound asked.
     const bool u64 = req->k > 32;
-    const size_t smem_budget = size_t(s->props.max_smem) - 16 -
+    const size_t smem_budget = size_t(s->props.max_smem) - kBatchHeaderBytes -
                                size_t(kThreads / 32) * warp_bytes(u64, false, tile_for(u64));
     uint64_t bound = req->table_bound ? req->table_bound : 8192;
     rmat_table *t = nullptr;

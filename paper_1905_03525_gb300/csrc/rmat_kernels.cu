@@ -2,7 +2,7 @@
 // launch logic.
 //
 // gen_tile: the per-edge sampling loop of arXiv 1905.03525, Sec. 2 (sampling-
-// loop fragment) for one warp tile of consecutive edges, two edges per lane:
+// loop fragment) for one warp tile of consecutive edges, several per lane:
 //   phase 1  one Philox4x32-10 block (4 words) per edge, up to 4 alias draws,
 //            path bits OR-ed into left-aligned row/column registers;
 //   phase 2  edges that still lack levels after 4 words are queued per warp

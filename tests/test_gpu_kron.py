@@ -44,6 +44,7 @@ CASES = [
     (3, 20, "variable", 4096, 60_000, 7 << 33),    # u32, 3^20 close to 2^32, large offset
     (3, 30, "variable", 4096, 40_000, 5),          # u64
     (3, 40, "variable", 8192, 20_000, 0),          # deepest k, long paths
+    (3, 20, "variable", 8192, 50_000, 3),          # u32 IDs, 9-level paths, 197 KB table
     (4, 16, "variable", 2000, 30_000, 1),          # n0^k = 2^32 exactly: u32
     (5, 13, "fixed", 2, 30_000, 3),
     (16, 8, "variable", 5000, 30_000, 0),          # 16^8 = 2^32

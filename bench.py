@@ -193,7 +193,7 @@ def cpu_baseline(total_edges: int):
     for th in threads:
         th.join()
     dt = time.perf_counter() - t0
-    return {"value": total_edges / dt, "unit": "edges/s", "cores": cores, "kind": "oracle",
+    return {"value": total_edges / dt, "unit": "edges/s", "cores": cores, "kind": "oracle", "seconds": dt,
             "sample": f"edges 0..{total_edges - 1} of the same graph (k=26, bound 2^12, seed 1), "
                       f"{cores} threads, {dt:.1f} s wall"}
 
@@ -209,11 +209,12 @@ def run_reference(args):
     for _ in range(max(1, args.steps)):
         vals.append(cpu_baseline(n // max(1, args.steps)))
     v = statistics.median([x["value"] for x in vals])
+    step_ms = 1e3 * statistics.median([x.pop("seconds") for x in vals])
     cb = dict(vals[-1])
     cb["value"] = v
     cb["sample"] = f"{args.steps} steps of {n // max(1, args.steps)} edges each: " + cb["sample"]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "edges/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "k": K, "m": 1 << LOG2M, "table_bound": BOUND},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": "edges/s", "h2d_bytes_per_step": 0,
@@ -322,6 +323,7 @@ def run_ours(args):
     cb = None
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(args.cpu_sample_edges)
+        cb.pop("seconds")
     cs = clocks.summary()
     line = {
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,

@@ -78,23 +78,20 @@ __device__ __forceinline__ dev::Group<SMEM> group0(const Job &J, uint32_t sblob)
 }
 
 // Where a tile's Philox round keys come from: the job's schedule in a kernel
-// parameter (uint32_t[20]: constant-bank operands of the xors), the schedule
-// staged in shared memory (SharedKeys: five broadcast loads per block), or
-// the job's key, advanced in registers (RegKeys).
+// parameter (uint32_t[20]: constant-bank operands of the xors; k_alias) or
+// the schedule staged in shared memory (SharedKeys: five broadcast loads per
+// block; k_batch, whose job is a register copy).
 struct SharedKeys {
     uint32_t addr;
 };
-struct RegKeys {};
 template <class K>
-constexpr bool kConstKeys = !std::is_same<K, SharedKeys>::value && !std::is_same<K, RegKeys>::value;
+constexpr bool kConstKeys = !std::is_same<K, SharedKeys>::value;
 
 // Philox block q of edge e under the job's key.
 template <class K>
-__device__ __forceinline__ uint4 edge_block(const Job &J, const K &ks, uint32_t q, uint64_t e) {
+__device__ __forceinline__ uint4 edge_block(const K &ks, uint32_t q, uint64_t e) {
     if constexpr (std::is_same<K, SharedKeys>::value)
         return dev::philox_sks(q, 0u, uint32_t(e), uint32_t(e >> 32), ks.addr);
-    else if constexpr (std::is_same<K, RegKeys>::value)
-        return dev::philox(q, 0u, uint32_t(e), uint32_t(e >> 32), J.key0, J.key1);
     else
         return dev::philox_ks(q, 0u, uint32_t(e), uint32_t(e >> 32), ks);
 }
@@ -206,7 +203,7 @@ __device__ __forceinline__ uint32_t phase1(const Job &J, const K &ks, const Scra
         Acc a[E];
 #pragma unroll
         for (int q = 0; q < E; ++q) {
-            w[q] = edge_block(J, ks, 0u, ebase + (it + q) * 32 + lane);
+            w[q] = edge_block(ks, 0u, ebase + (it + q) * 32 + lane);
             a[q].clear();
             if constexpr (PRE) {
                 // batched jobs may start below the top level (a partition tile)
@@ -272,7 +269,7 @@ __device__ __forceinline__ void gen_tile(const Job &J, const K &ks, const Scramb
                 uint32_t ws[EL][4];
 #pragma unroll
                 for (int x = 0; x < EL; ++x) {
-                    const uint4 w = edge_block(J, ks, uint32_t(q), ebase + base + 32 * x + lane);
+                    const uint4 w = edge_block(ks, uint32_t(q), ebase + base + 32 * x + lane);
                     ws[x][0] = w.x;
                     ws[x][1] = w.y;
                     ws[x][2] = w.z;
@@ -346,7 +343,7 @@ __device__ __forceinline__ void gen_tile(const Job &J, const K &ks, const Scramb
                 // another draw (a warp-uniform branch)
                 for (uint32_t q = 1; q <= 17; ++q) {
                     if (!__any_sync(0xffffffffu, acc.filled < uk)) break;
-                    const uint4 w = edge_block(J, ks, q, e);
+                    const uint4 w = edge_block(ks, q, e);
                     if (U64) {
                         if (acc.filled < uk) dev::draw<FMT, SMEM>(G0, w.x, acc);
                     } else {
@@ -929,11 +926,9 @@ Job make_job(const rmat_table *t, const uint32_t *dblob, bool smem, uint64_t see
     J.ngroups = int(t->groups.size());
     J.levels = t->per_level ? 1u : 0u;
     J.flags = t->flags;
-    J.key0 = uint32_t(seed);
-    J.key1 = uint32_t(seed >> 32);
     for (int r = 0; r < 10; ++r) {
-        J.ks[2 * r] = J.key0 + uint32_t(r) * 0x9E3779B9u;
-        J.ks[2 * r + 1] = J.key1 + uint32_t(r) * 0xBB67AE85u;
+        J.ks[2 * r] = uint32_t(seed) + uint32_t(r) * 0x9E3779B9u;
+        J.ks[2 * r + 1] = uint32_t(seed >> 32) + uint32_t(r) * 0xBB67AE85u;
     }
     J.e0 = e0;
     J.count = count;

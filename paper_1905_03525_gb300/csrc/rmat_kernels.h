@@ -25,8 +25,7 @@ struct Job {
     int draws1;            // draws in phase 1 (<= 4)
     int ngroups;
     unsigned flags;
-    uint32_t key0, key1;   // Philox key = seed
-    uint32_t ks[20];       // round keys: key + r * (Weyl constants), r = 0..9
+    uint32_t ks[20];       // Philox round keys: seed + r * (Weyl constants), r = 0..9
     uint64_t e0, count;
     void *out;
     uint32_t fmt;          // image format

@@ -86,7 +86,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-edges", type=int, default=1 << 27)
-    ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5", "part", "kron", "tablebuild"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5", "part", "kron", "tablebuild", "fig1"],
+                    default="c2",
                     help="c2 (default): the contract line; c1/c3/c4/c5: the other configurations, one JSON line each")
     ap.add_argument("--log2m", type=int, default=LOG2M,
                     help="c2: edges per GPU = 2^log2m (default 30; smaller only for profiling captures)")
@@ -588,6 +589,43 @@ def run_kron(args):
           flush=True)
 
 
+SKEWED = (0.9, 0.025, 0.025, 0.05)  # the skewed parameters of Sec. 4
+
+
+def run_fig1(args):
+    """The experiment of Fig. 1 on one GB300: edges/s against table size for
+    variable-length tables (bounds 2^8..2^20) and fixed-length tables (l =
+    4..10), with the Graph 500 and the skewed parameters of Sec. 4, n = 2^30
+    vertices, 2^28 edges per launch (u32).  Tables up to ~2^14 columns are
+    staged in shared memory; larger ones are read from global memory (L2)."""
+    import torch
+    import paper_1905_03525_gb300 as rm
+    k, m = 30, 1 << min(args.log2m, 28)
+    out = rm.empty_edges(m, k)
+    s = torch.cuda.Stream()
+    rows = []
+    for pname, abcd in (("graph500", G500), ("skewed", SKEWED)):
+        cases = [("variable", b, lambda b=b: rm.rmat_build_table(*abcd, k, b)) for b in
+                 (1 << 8, 1 << 10, 1 << 12, 1 << 14, 1 << 16, 1 << 18, 1 << 20)]
+        cases += [("fixed", ell, lambda ell=ell: rm.rmat_build_table_fixed(*abcd, k, ell)) for ell in range(4, 11)]
+        for kind, x, build in cases:
+            table = build()
+            info = rm.rmat_table_info(table)
+            with torch.cuda.stream(s):
+                for _ in range(max(2, args.warmup)):
+                    rm.rmat_generate(table, SEED, 0, m, out, s)
+                dt = _events_time(lambda: rm.rmat_generate(table, SEED, 0, m, out, s), s, max(3, min(args.steps, 5)))
+            rm.rmat_check_device_errors()
+            rows.append({"params": pname, "kind": kind, ("bound" if kind == "variable" else "ell"): x,
+                         "entries": info["entries"], "image_bytes": info["device_image_bytes"],
+                         "edges_per_s": m / dt, "ns_per_edge_per_sm": dt / m * 1e9 * torch.cuda.get_device_properties(
+                             torch.cuda.current_device()).multi_processor_count})
+            table.free()
+    print(json.dumps({"workload": "fig1", "config": {"workload": f"R-MAT k={k}, 2^{m.bit_length() - 1} edges per "
+                      f"launch, seed {SEED}, u32; Graph 500 parameters {G500} and skewed {SKEWED}; variable bounds "
+                      "2^8..2^20, fixed l = 4..10"}, "metric": "edges/s", "rows": rows}), flush=True)
+
+
 def run_tablebuild(args):
     """Variable-length table construction (G500 parameters, k = 26) on the host
     (rmat_build_table) and on the GPU (rmat_build_table_gpu, identical
@@ -637,6 +675,8 @@ def main():
         run_kron(args)
     elif args.workload == "tablebuild":
         run_tablebuild(args)
+    elif args.workload == "fig1":
+        run_fig1(args)
     elif args.workload == "c5":
         from paper_1905_03525_gb300 import serve
         serve.bench(args)

@@ -4,13 +4,17 @@
 //
 // The first occurrence of every (row, col), in the order of the input, stays;
 // the survivors are compacted to the front in that order, so the result is a
-// pure function of the input array.  Four passes over the edges:
-//   1. insert key = row * 2^k + col into an open-addressing hash table
-//      (linear probing, atomicCAS on 64-bit keys), remembering the slot;
-//   2. atomicMin the edge's index into its slot's first-index word;
-//   3. an edge survives iff it holds its slot's first index; per-block counts;
-//   4. exclusive scan of the block counts, then an ordered block-local
-//      compaction (warp ballots) into a second buffer, copied back.
+// pure function of the input array.  Three passes over the edges:
+//   1. insert key = row * 2^k + col into an open-addressing hash table of
+//      16-byte slots {key, first index} (linear probing): one 128-bit CAS
+//      claims a free slot with the edge's key and index; an edge that finds
+//      its key already there lowers the slot's first index with atomicMin
+//      when its own index is smaller; each edge remembers its slot;
+//   2. an edge survives iff it holds its slot's first index: one flag byte
+//      per edge and per-chunk counts;
+//   3. exclusive scan of the chunk counts, then an ordered chunk-local
+//      compaction driven by the flags (sequential reads) into a second
+//      buffer, copied back.
 // The table has at least twice as many slots as edges; every probe loop is
 // bounded by the table size and reports an error instead of spinning.
 #include <cuda_runtime.h>
@@ -27,6 +31,7 @@ namespace {
 constexpr uint64_t kEmpty = ~uint64_t(0);
 constexpr int kBlock = 1024;
 constexpr int kPerThread = 4;                      // edges per thread in the compaction
+static_assert(kPerThread == 4, "k_dedup_count stores a thread's flags as one 4-byte word");
 constexpr uint64_t kChunk = uint64_t(kBlock) * kPerThread;
 
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
@@ -43,15 +48,36 @@ __device__ __forceinline__ uint64_t edge_key(const uint2 *e, uint64_t i, int k) 
     return (uint64_t(v.x) << k) | v.y;
 }
 
-__global__ void k_dedup_insert(const uint2 *edges, uint64_t n, int k, unsigned long long *keys, uint64_t mask,
+// 128-bit compare-and-swap (PTX atom.cas.b128, sm_90 and later) on the
+// 16-byte-aligned pair {lo at addr, hi at addr + 8}; returns the old pair.
+__device__ __forceinline__ void cas128(unsigned long long *addr, uint64_t cmp_lo, uint64_t cmp_hi, uint64_t new_lo,
+                                       uint64_t new_hi, uint64_t &old_lo, uint64_t &old_hi) {
+    asm volatile(
+        "{\n\t.reg .b128 c, n, o;\n\t"
+        "mov.b128 c, {%2, %3};\n\t"
+        "mov.b128 n, {%4, %5};\n\t"
+        "atom.global.cas.b128 o, [%6], c, n;\n\t"
+        "mov.b128 {%0, %1}, o;\n\t}"
+        : "=l"(old_lo), "=l"(old_hi)
+        : "l"(cmp_lo), "l"(cmp_hi), "l"(new_lo), "l"(new_hi), "l"(addr)
+        : "memory");
+}
+
+// Slot h of the table: tab[2h] = key (kEmpty when free), tab[2h + 1] = the
+// smallest index of an edge with that key (all ones while free).  A slot
+// leaves the free state once, by the CAS that writes both words; after that
+// only its index word changes, by atomicMin.
+__global__ void k_dedup_insert(const uint2 *edges, uint64_t n, int k, unsigned long long *tab, uint64_t mask,
                                uint32_t *slot_of, unsigned *err) {
     for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x) {
         const uint64_t key = edge_key(edges, i, k);
         uint64_t h = mix64(key) & mask;
         bool placed = false;
         for (uint64_t probe = 0; probe <= mask; ++probe) {  // at most one pass over the table
-            const unsigned long long old = atomicCAS(keys + h, (unsigned long long)kEmpty, (unsigned long long)key);
-            if (old == kEmpty || old == key) {
+            uint64_t old_key, old_first;
+            cas128(tab + 2 * h, kEmpty, kEmpty, key, i, old_key, old_first);
+            if (old_key == kEmpty || old_key == key) {
+                if (old_key == key && i < old_first) atomicMin(tab + 2 * h + 1, (unsigned long long)i);
                 slot_of[i] = uint32_t(h);
                 placed = true;
                 break;
@@ -62,22 +88,28 @@ __global__ void k_dedup_insert(const uint2 *edges, uint64_t n, int k, unsigned l
     }
 }
 
-__global__ void k_dedup_first(uint64_t n, const uint32_t *slot_of, unsigned long long *first) {
-    for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x)
-        atomicMin(first + slot_of[i], (unsigned long long)i);
-}
-
 // Survivor flags of chunk `c` (kChunk edges, thread t holds edges
-// c*kChunk + t*kPerThread + j) and the chunk's count.
+// c*kChunk + t*kPerThread + j; one byte per edge) and the chunk's count.
 __global__ void __launch_bounds__(kBlock) k_dedup_count(uint64_t n, const uint32_t *slot_of,
-                                                        const unsigned long long *first, uint32_t *chunk_count) {
+                                                        const unsigned long long *tab, uint8_t *flag,
+                                                        uint32_t *chunk_count) {
     __shared__ uint32_t warp_sum[kBlock / 32];
     const uint64_t base = blockIdx.x * kChunk + uint64_t(threadIdx.x) * kPerThread;
-    uint32_t c = 0;
+    uint32_t c = 0, bits = 0;
 #pragma unroll
     for (int j = 0; j < kPerThread; ++j) {
         const uint64_t i = base + j;
-        if (i < n && first[slot_of[i]] == i) ++c;
+        if (i < n && tab[2 * uint64_t(slot_of[i]) + 1] == i) {
+            ++c;
+            bits |= 1u << (8 * j);
+        }
+    }
+    if (base + kPerThread <= n) {
+        *reinterpret_cast<uint32_t *>(flag + base) = bits;  // kPerThread == 4 flag bytes
+    } else {
+#pragma unroll
+        for (int j = 0; j < kPerThread; ++j)
+            if (base + j < n) flag[base + j] = uint8_t(bits >> (8 * j));
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
@@ -128,9 +160,8 @@ __global__ void __launch_bounds__(kBlock) k_dedup_scan(uint32_t *counts, uint64_
 }
 
 // Ordered compaction of chunk `c` to dst starting at offsets[c].
-__global__ void __launch_bounds__(kBlock) k_dedup_compact(const uint2 *edges, uint64_t n, const uint32_t *slot_of,
-                                                          const unsigned long long *first, const uint32_t *offsets,
-                                                          uint2 *dst) {
+__global__ void __launch_bounds__(kBlock) k_dedup_compact(const uint2 *edges, uint64_t n, const uint8_t *flag,
+                                                          const uint32_t *offsets, uint2 *dst) {
     __shared__ uint32_t warp_base[kBlock / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t base = blockIdx.x * kChunk + uint64_t(threadIdx.x) * kPerThread;
@@ -138,7 +169,7 @@ __global__ void __launch_bounds__(kBlock) k_dedup_compact(const uint2 *edges, ui
 #pragma unroll
     for (int j = 0; j < kPerThread; ++j) {
         const uint64_t i = base + j;
-        if (i < n && first[slot_of[i]] == i) {
+        if (i < n && flag[i]) {
             keep |= 1u << j;
             ++c;
         }
@@ -189,11 +220,12 @@ extern "C" rmat_status rmat_dedup_edges(void *edges, uint64_t count, int k, uint
     uint64_t slots = 1;
     while (slots < 2 * count) slots <<= 1;
     const uint64_t chunks = (count + kChunk - 1) / kChunk;
-    // scratch: keys and first indices per slot, slot per edge, chunk counts,
-    // the compacted copy, the total and an error word
-    const size_t off_first = slots * 8;
-    const size_t off_slot = off_first + slots * 8;
-    const size_t off_cnt = off_slot + ((count * 4 + 255) & ~size_t(255));
+    // scratch: the table (key, first index) per slot, slot per edge, flag
+    // byte per edge, chunk counts, the compacted copy, the total and an error
+    // word
+    const size_t off_slot = slots * 16;
+    const size_t off_flag = off_slot + ((count * 4 + 255) & ~size_t(255));
+    const size_t off_cnt = off_flag + ((count + 255) & ~size_t(255));
     const size_t off_dst = off_cnt + ((chunks * 4 + 255) & ~size_t(255));
     const size_t off_tot = off_dst + count * 8;
     const size_t bytes = off_tot + 16;
@@ -202,24 +234,22 @@ extern "C" rmat_status rmat_dedup_edges(void *edges, uint64_t count, int k, uint
         cudaGetLastError();
         return fail(RMAT_ERR_OUT_OF_MEMORY, "device scratch for duplicate removal");
     }
-    auto *keys = reinterpret_cast<unsigned long long *>(scratch);
-    auto *first = reinterpret_cast<unsigned long long *>(scratch + off_first);
+    auto *tab = reinterpret_cast<unsigned long long *>(scratch);
     auto *slot_of = reinterpret_cast<uint32_t *>(scratch + off_slot);
+    auto *flag = reinterpret_cast<uint8_t *>(scratch + off_flag);
     auto *cnt = reinterpret_cast<uint32_t *>(scratch + off_cnt);
     auto *dst = reinterpret_cast<uint2 *>(scratch + off_dst);
     auto *total = reinterpret_cast<unsigned long long *>(scratch + off_tot);
     auto *err = reinterpret_cast<unsigned *>(scratch + off_tot + 8);
     const uint2 *src = static_cast<const uint2 *>(edges);
     const int grid = props.sms * 8;
-    cudaError_t e = cudaMemsetAsync(keys, 0xFF, slots * 8, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(first, 0xFF, slots * 8, stream);
+    cudaError_t e = cudaMemsetAsync(tab, 0xFF, slots * 16, stream);  // kEmpty keys, first = max
     if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 4, stream);
     if (e == cudaSuccess) {
-        k_dedup_insert<<<grid, 256, 0, stream>>>(src, count, k, keys, slots - 1, slot_of, err);
-        k_dedup_first<<<grid, 256, 0, stream>>>(count, slot_of, first);
-        k_dedup_count<<<unsigned(chunks), kBlock, 0, stream>>>(count, slot_of, first, cnt);
+        k_dedup_insert<<<grid, 256, 0, stream>>>(src, count, k, tab, slots - 1, slot_of, err);
+        k_dedup_count<<<unsigned(chunks), kBlock, 0, stream>>>(count, slot_of, tab, flag, cnt);
         k_dedup_scan<<<1, kBlock, 0, stream>>>(cnt, chunks, total);
-        k_dedup_compact<<<unsigned(chunks), kBlock, 0, stream>>>(src, count, slot_of, first, cnt, dst);
+        k_dedup_compact<<<unsigned(chunks), kBlock, 0, stream>>>(src, count, flag, cnt, dst);
         e = cudaGetLastError();
     }
     unsigned long long host_total = 0;

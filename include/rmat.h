@@ -343,9 +343,11 @@ void rmat_free_partition(rmat_partition *p);
  * the output of rmat_generate_partition); the first occurrence of every
  * (row, col) in array order is kept and the survivors are compacted to the
  * front in that order; *unique receives their number.  Synchronous on
- * `stream`; count <= 2^31; allocates and frees ~(32 x 2 + 12) bytes of
- * device scratch per edge.  Errors: RMAT_ERR_INVALID_ARGUMENT (k, count,
- * alignment), RMAT_ERR_OUT_OF_MEMORY, RMAT_ERR_CUDA. */
+ * `stream`; count <= 2^31; allocates and frees 45 to 77 bytes of device
+ * scratch per edge (a hash table of 16-byte slots, a power of two at least
+ * twice the edge count, and 13 bytes per edge).  Errors:
+ * RMAT_ERR_INVALID_ARGUMENT (k, count, alignment), RMAT_ERR_OUT_OF_MEMORY,
+ * RMAT_ERR_CUDA. */
 rmat_status rmat_dedup_edges(void *edges, uint64_t count, int k, uint64_t *unique, rmat_stream_t stream);
 
 /* ---------------------------------------------------------------------- */

@@ -90,7 +90,8 @@ def parse():
                     default="c2",
                     help="c2 (default): the contract line; c1/c3/c4/c5: the other configurations, one JSON line each")
     ap.add_argument("--log2m", type=int, default=LOG2M,
-                    help="c2: edges per GPU = 2^log2m (default 30; smaller only for profiling captures)")
+                    help="c2: edges per GPU = 2^log2m (default 30; smaller only for profiling captures); "
+                         "c3: chunk size; part, kron: edges; fig1: edges per launch (at most 2^28)")
     ap.add_argument("--graphs", type=int, default=4096, help="c4: number of graphs")
     ap.add_argument("--tile-levels", type=int, default=5, help="part: tiles of 2^(k-t) x 2^(k-t) vertices")
     ap.add_argument("--wave-gib", type=float, default=48.0, help="c4: output budget per batched launch")
@@ -399,7 +400,7 @@ def run_c3(args):
     import paper_1905_03525_gb300 as rm
     from paper_1905_03525_gb300 import autotune
     from paper_1905_03525_gb300.workloads import noisy_levels
-    k, chunk, nchunks = 34, 1 << 30, 32
+    k, chunk, nchunks = 34, 1 << min(args.log2m, 30), 32  # smaller chunks only for profiling captures
     P = noisy_levels(k)
     choice = autotune.tune_levels(k, P, rm.RMAT_UNDIRECTED)
     t = rm.rmat_build_table_levels(P, k, choice["ell"], rm.RMAT_UNDIRECTED)
@@ -420,9 +421,10 @@ def run_c3(args):
     dt = a.elapsed_time(b) / 1e3
     peak, src = measured_peak()
     gbs = 16.0 * chunk * nchunks / dt / 1e9
-    print(json.dumps({"workload": "c3", "config": {"workload": "R-MAT k=34, m=2^35 streamed in 32 chunks of 2^30 "
-                      "edges into one 16 GiB buffer, u64 pairs, undirected, per-level noise +-0.05 on "
-                      "0.57,0.19,0.19,0.05", "ell": choice["ell"], "launch": list(shape)},
+    lc = chunk.bit_length() - 1
+    print(json.dumps({"workload": "c3", "config": {"workload": f"R-MAT k=34, m=2^{lc + 5} streamed in 32 chunks of "
+                      f"2^{lc} edges into one {16 * chunk >> 30} GiB buffer, u64 pairs, undirected, per-level noise "
+                      "+-0.05 on 0.57,0.19,0.19,0.05", "ell": choice["ell"], "launch": list(shape)},
                       "metric": "edges/s", "value": chunk * nchunks / dt, "seconds": dt,
                       "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                                    "peak_source": src},

@@ -102,13 +102,16 @@ def _param_key(abcd) -> str:
 
 
 def tune_table(k: int, abcd, sample_edges: int = 1 << 24, bounds=BOUNDS, ells=ELLS, seed: int = 1,
-               max_blob_bytes: int = 160 * 1024):
+               max_blob_bytes: int = 160 * 1024, batched: bool = False):
     """Fastest table for (k, a, b, c, d): a variable-length table with one of
     `bounds`, or a fixed-length table with one of `ells`, among those whose
     device blob is at most `max_blob_bytes` (what the launch can stage in
-    shared memory).  Returns a dict {"kind": "variable"|"fixed",
-    "bound"|"ell": ..., "edges_per_s": ...}."""
-    key = f"table:k{k}:p{_param_key(abcd)}:s{max_blob_bytes}"
+    shared memory).  batched: time each candidate in the batched kernel (a
+    one-graph batch) instead of the single-graph kernel -- the two keep
+    different numbers of edges in flight per lane, which can change the
+    ranking.  Returns a dict {"kind": "variable"|"fixed", "bound"|"ell": ...,
+    "edges_per_s": ...}."""
+    key = f"table:k{k}:p{_param_key(abcd)}:s{max_blob_bytes}" + (":batched" if batched else "")
     cached = _load().get(key)
     if cached:
         return cached
@@ -119,7 +122,14 @@ def tune_table(k: int, abcd, sample_edges: int = 1 << 24, bounds=BOUNDS, ells=EL
         t = rmat_build_table(*abcd, k, x) if kind == "variable" else rmat_build_table_fixed(*abcd, k, x)
         if rmat_table_info(t)["device_image_bytes"] > max_blob_bytes:
             continue  # would not fit shared memory beside the warp tiles
-        dt = time_launches(lambda s: rmat_generate(t, seed, 0, sample_edges, out, s))
+        if batched:
+            b = rmat_batch_create()
+            rmat_batch_add(b, t, seed, 0, sample_edges, out)
+            rmat_batch_prepare(b)
+            dt = time_launches(lambda s: rmat_batch_launch(b, s), reps=5)
+            b.free()
+        else:
+            dt = time_launches(lambda s: rmat_generate(t, seed, 0, sample_edges, out, s))
         rate = sample_edges / dt
         if best is None or rate > best["edges_per_s"]:
             best = {"kind": kind, ("bound" if kind == "variable" else "ell"): x, "edges_per_s": rate}
@@ -179,12 +189,12 @@ def batch_blob_budget(threads: int = 1024, tile: int = 512, u64: bool = False) -
     return smem - header - (threads // 32) * per_warp
 
 
-def plan_batch(graphs, representative=None, sample_edges: int = 1 << 22):
+def plan_batch(graphs, representative=None, sample_edges: int = 1 << 24):
     """Table choice for every graph of a batch: the tuner runs once per k on
     representative parameters (default: the mean of the graphs' parameters),
-    among tables that the batched kernel can stage in shared memory, then each
-    graph gets a table of that kind sized for its edge count.  Returns the
-    tables and the per-k choices."""
+    timing the batched kernel itself on tables that it can stage in shared
+    memory, then each graph gets a table of that kind sized for its edge
+    count.  Returns the tables and the per-k choices."""
     P = np.asarray([g["abcd"] for g in graphs], np.float64)
     rep = tuple(float(x) for x in (representative if representative is not None else P.mean(axis=0)))
     rep = tuple(x / sum(rep) for x in rep)
@@ -193,7 +203,8 @@ def plan_batch(graphs, representative=None, sample_edges: int = 1 << 22):
     for g in graphs:
         k = g["k"]
         if k not in choices:
-            choices[k] = tune_table(k, rep, sample_edges=sample_edges, max_blob_bytes=batch_blob_budget())
+            choices[k] = tune_table(k, rep, sample_edges=sample_edges, max_blob_bytes=batch_blob_budget(),
+                                    batched=True)
         tables.append(build_tuned_table(k, g["abcd"], g["m"], choices[k]))
     return tables, choices
 

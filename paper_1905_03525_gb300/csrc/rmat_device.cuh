@@ -231,6 +231,40 @@ __device__ __forceinline__ void draw(const Group<SMEM> &G, uint32_t u, Acc &acc)
     }
 }
 
+// The same draw from a table of fixed-length paths (every entry has exactly
+// L levels, 1 <= L <= 12: the per-level tables), returning the path's row and
+// column bits right-aligned in r and c.
+template <int FMT, bool SMEM>
+__device__ __forceinline__ void draw_fixed(const Group<SMEM> &G, uint32_t u, uint32_t L, uint32_t &r,
+                                           uint32_t &c) {
+    const uint32_t j = __umulhi(u, G.mulb);
+    const uint32_t s = 32u - L;
+    if constexpr (SMEM) {
+        const uint32_t off = 4u * j;
+        const bool keep = u < lds32(G.sA + off);
+        if constexpr (FMT == 0) {
+            const uint32_t x = lds32((keep ? G.sBs : G.sBa) + off);
+            r = x >> s;
+            c = (x << 19) >> s;
+        } else {
+            const uint4 v = lds128((keep ? G.sBs : G.sBa) + 4u * off);
+            r = v.x >> s;
+            c = v.y >> s;
+        }
+    } else {
+        const bool keep = u < __ldg(G.gA + j);
+        if constexpr (FMT == 0) {
+            const uint32_t x = __ldg((keep ? G.gBs : G.gBa) + j);
+            r = x >> s;
+            c = (x << 19) >> s;
+        } else {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(keep ? G.gBs : G.gBa) + j);
+            r = v.x >> s;
+            c = v.y >> s;
+        }
+    }
+}
+
 // --------------------------------------------------------------------------
 // PTX helpers: mbarrier, TMA bulk copies (global <-> shared), proxy fences.
 // --------------------------------------------------------------------------

@@ -257,14 +257,21 @@ __device__ __forceinline__ void gen_tile(const Job &J, const K &ks, const Scramb
     __syncwarp();
 
     if constexpr (LEVELS) {
+        // Per-level tables hold fixed-length paths: every path of group g has
+        // L_g = b_g / 2 levels (4^L_g columns) and the groups' lengths add up
+        // to k.  So a draw appends its bits right-aligned, row = row * 2^L_g +
+        // bits, with a shift the whole warp shares, and each word is
+        // left-aligned once, for the store epilogue, after the last group.
         // EL edges per lane (idx, idx + 32, ...) share each group's descriptor;
         // two in the single-graph kernel, one in the batched kernel, whose
         // register copy of the job leaves no room for a second.
         constexpr int EL = kConstKeys<K> ? 2 : 1;
+        using Word = typename AccT<U64>::word;
+        constexpr uint32_t WB = U64 ? 64u : 32u;
         for (uint32_t base = 0; base < n; base += 32 * EL) {
-            Acc a[EL];
+            Word row[EL], col[EL];
 #pragma unroll
-            for (int q = 0; q < EL; ++q) a[q].clear();
+            for (int q = 0; q < EL; ++q) row[q] = col[q] = 0;
             for (int q = 0; 4 * q < J.ngroups; ++q) {
                 uint32_t ws[EL][4];
 #pragma unroll
@@ -289,15 +296,27 @@ __device__ __forceinline__ void gen_tile(const Job &J, const K &ks, const Scramb
                         } else {
                             Gg = dev::group<SMEM>(sblob, gblob, uint32_t(g));
                         }
+                        const uint32_t L = uint32_t(31 - __clz(Gg.mulb)) >> 1;  // mulb = 2^(2 L)
 #pragma unroll
-                        for (int x = 0; x < EL; ++x) dev::draw<FMT, SMEM>(Gg, ws[x][i], a[x]);
+                        for (int x = 0; x < EL; ++x) {
+                            uint32_t r, c;
+                            dev::draw_fixed<FMT, SMEM>(Gg, ws[x][i], L, r, c);
+                            row[x] = (row[x] << L) | r;
+                            col[x] = (col[x] << L) | c;
+                        }
                     }
                 }
             }
 #pragma unroll
             for (int x = 0; x < EL; ++x) {
                 const uint32_t idx = base + 32 * x + lane;
-                if (idx < n) put_final<U64, EPI>(stage, idx, a[x], J, S);
+                if (idx < n) {
+                    Acc a;
+                    a.row = row[x] << (WB - uk);
+                    a.col = col[x] << (WB - uk);
+                    a.filled = uk;
+                    put_final<U64, EPI>(stage, idx, a, J, S);
+                }
             }
         }
     } else {

@@ -126,6 +126,15 @@ __device__ __forceinline__ uint64_t scramble_id(typename AccT<U64>::word X, cons
     return uint64_t(X >> (W - uint32_t(J.k)));
 }
 
+// w * 2^L + bits for 1 <= L <= 12 (a per-level group); the 64-bit form
+// shifts its two halves with one funnel shift, the amount being known to be
+// below 32.
+__device__ __forceinline__ uint32_t append_fixed(uint32_t w, uint32_t bits, uint32_t L) { return (w << L) | bits; }
+__device__ __forceinline__ uint64_t append_fixed(uint64_t w, uint32_t bits, uint32_t L) {
+    const uint32_t lo = uint32_t(w), hi = uint32_t(w >> 32);
+    return (uint64_t(__funnelshift_l(lo, hi, L)) << 32) | ((lo << L) | bits);
+}
+
 // Store-epilogue variants (template argument EPI): bit 0 mirrors the edge to
 // (min, max); bit 1 relabels every edge; bit 2 relabels when the job's flags
 // ask for it (a batched launch mixes jobs with and without relabelling).
@@ -146,6 +155,26 @@ __device__ __forceinline__ void put_final(uint32_t stage, uint32_t idx, const ty
     } else {
         r = acc.out_row(J.k);
         c = acc.out_col(J.k);
+    }
+    if ((EPI & kEpiUndir) && r > c) {
+        const uint64_t t = r;
+        r = c;
+        c = t;
+    }
+    put_pair<U64>(stage, idx, r, c);
+}
+
+// The same for IDs already right-aligned (row, col < 2^k): relabelling takes
+// them left-aligned, the plain store as they are.
+template <bool U64, int EPI>
+__device__ __forceinline__ void put_final_right(uint32_t stage, uint32_t idx, typename AccT<U64>::word row,
+                                                typename AccT<U64>::word col, const Job &J, const Scramble &S) {
+    using Word = typename AccT<U64>::word;
+    constexpr uint32_t W = U64 ? 64u : 32u;
+    uint64_t r = row, c = col;
+    if (relabel<EPI>(J)) {
+        r = scramble_id<U64>(Word(row << (W - uint32_t(J.k))), J, S);
+        c = scramble_id<U64>(Word(col << (W - uint32_t(J.k))), J, S);
     }
     if ((EPI & kEpiUndir) && r > c) {
         const uint64_t t = r;
@@ -260,14 +289,13 @@ __device__ __forceinline__ void gen_tile(const Job &J, const K &ks, const Scramb
         // Per-level tables hold fixed-length paths: every path of group g has
         // L_g = b_g / 2 levels (4^L_g columns) and the groups' lengths add up
         // to k.  So a draw appends its bits right-aligned, row = row * 2^L_g +
-        // bits, with a shift the whole warp shares, and each word is
-        // left-aligned once, for the store epilogue, after the last group.
+        // bits, with a shift the whole warp shares, and the words leave as
+        // they are (left-aligned only for relabelling).
         // EL edges per lane (idx, idx + 32, ...) share each group's descriptor;
         // two in the single-graph kernel, one in the batched kernel, whose
         // register copy of the job leaves no room for a second.
         constexpr int EL = kConstKeys<K> ? 2 : 1;
         using Word = typename AccT<U64>::word;
-        constexpr uint32_t WB = U64 ? 64u : 32u;
         for (uint32_t base = 0; base < n; base += 32 * EL) {
             Word row[EL], col[EL];
 #pragma unroll
@@ -301,8 +329,8 @@ __device__ __forceinline__ void gen_tile(const Job &J, const K &ks, const Scramb
                         for (int x = 0; x < EL; ++x) {
                             uint32_t r, c;
                             dev::draw_fixed<FMT, SMEM>(Gg, ws[x][i], L, r, c);
-                            row[x] = (row[x] << L) | r;
-                            col[x] = (col[x] << L) | c;
+                            row[x] = append_fixed(row[x], r, L);
+                            col[x] = append_fixed(col[x], c, L);
                         }
                     }
                 }
@@ -310,13 +338,7 @@ __device__ __forceinline__ void gen_tile(const Job &J, const K &ks, const Scramb
 #pragma unroll
             for (int x = 0; x < EL; ++x) {
                 const uint32_t idx = base + 32 * x + lane;
-                if (idx < n) {
-                    Acc a;
-                    a.row = row[x] << (WB - uk);
-                    a.col = col[x] << (WB - uk);
-                    a.filled = uk;
-                    put_final<U64, EPI>(stage, idx, a, J, S);
-                }
+                if (idx < n) put_final_right<U64, EPI>(stage, idx, row[x], col[x], J, S);
             }
         }
     } else {

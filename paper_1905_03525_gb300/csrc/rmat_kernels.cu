@@ -223,10 +223,10 @@ __device__ __forceinline__ uint32_t phase1(const Job &J, const K &ks, const Scra
     };
     // E edges per lane in flight (edges it*32 + lane, (it+1)*32 + lane, ...):
     // their independent Philox chains and table loads overlap.  Four pays off
-    // in the single-graph kernel for compact entries, u32 IDs and the plain
-    // epilogue; elsewhere two (more would spill, or measured slower in the
+    // in the single-graph kernel for compact entries and u32 IDs (plain or
+    // relabelled); elsewhere two (more would spill, or measured slower in the
     // batched kernel).
-    constexpr int E = (kConstKeys<K> && FMT == 0 && !U64 && !(EPI & (kEpiScr | kEpiScrFlag))) ? 4 : 2;
+    constexpr int E = (kConstKeys<K> && FMT == 0 && !U64 && !(EPI & kEpiScrFlag)) ? 4 : 2;
     for (uint32_t it = 0; it < iters; it += E) {
         uint4 w[E];
         Acc a[E];

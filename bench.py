@@ -38,10 +38,10 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic of one full-size k_alias launch of this workload (2^30 edges), from
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (1 pass) on the bench
 # command; valid only for the kernel sources whose hash is recorded with it.
-TRAFFIC = {"kernel_sha256_16": "c029e15e8211958b", "bytes_per_launch": 0.32e6 + 8.53e9}
+TRAFFIC = {"kernel_sha256_16": "b23a05095493de2d", "bytes_per_launch": 0.73e6 + 8.53e9}
 # Warp instructions per edge of the same kernel (smsp__inst_executed.sum / 2^26 on
 # the m=2^26 `ncu --set full` capture of this workload), valid for the same hash.
-INSTR = {"kernel_sha256_16": "c029e15e8211958b", "warp_instr_per_edge": 309336748 / 2 ** 26}
+INSTR = {"kernel_sha256_16": "b23a05095493de2d", "warp_instr_per_edge": 309336748 / 2 ** 26}
 KERNEL_SOURCES = ("paper_1905_03525_gb300/csrc/rmat_device.cuh", "paper_1905_03525_gb300/csrc/rmat_kernels.cu")
 
 

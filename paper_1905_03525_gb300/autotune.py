@@ -57,20 +57,22 @@ def _store(key: str, value) -> None:
         os.replace(tmp, _cache_path())
 
 
-def time_launches(fn, reps: int = 3, warmup: int = 1) -> float:
-    """Mean device time (s) of fn(stream) over `reps` back-to-back launches."""
+def time_launches(fn, reps: int = 5, warmup: int = 2) -> float:
+    """Median device time (s) of fn(stream) over `reps` back-to-back launches,
+    each timed by its own pair of events: one slow launch (a clock ramping up,
+    a neighbour on the GPU) cannot flip the choice between candidates whose
+    rates differ by a few per cent."""
     import torch
     s = torch.cuda.Stream()
     for _ in range(warmup):
         fn(s)
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record(s)
-    for _ in range(reps):
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        a.record(s)
         fn(s)
-    b.record(s)
+        b.record(s)
     s.synchronize()
-    return a.elapsed_time(b) / 1e3 / reps
+    return float(np.median([a.elapsed_time(b) for a, b in ev])) / 1e3
 
 
 def tune_launch(table, sample_edges: int = 1 << 26, shapes=LAUNCH_SHAPES, out=None, seed: int = 1):
@@ -126,7 +128,7 @@ def tune_table(k: int, abcd, sample_edges: int = 1 << 24, bounds=BOUNDS, ells=EL
             b = rmat_batch_create()
             rmat_batch_add(b, t, seed, 0, sample_edges, out)
             rmat_batch_prepare(b)
-            dt = time_launches(lambda s: rmat_batch_launch(b, s), reps=5)
+            dt = time_launches(lambda s: rmat_batch_launch(b, s), reps=7)
             b.free()
         else:
             dt = time_launches(lambda s: rmat_generate(t, seed, 0, sample_edges, out, s))

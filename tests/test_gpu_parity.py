@@ -245,7 +245,8 @@ def test_tables_with_different_shared_memory_needs_interleave():
 
 
 @pytest.mark.parametrize("kind,k,undirected", [("variable", 26, False), ("variable", 26, True), ("fixed", 16, False),
-                                               ("variable", 40, True), ("levels", 34, True), ("variable", 32, False)])
+                                               ("variable", 40, True), ("levels", 34, True), ("variable", 32, False),
+                                               ("levels", 20, False), ("levels", 32, True)])
 def test_scrambled_ids_match_oracle(kind, k, undirected):
     m = 30_000
     if kind == "variable":

@@ -28,6 +28,10 @@ from . import (rmat_batch_add, rmat_batch_create, rmat_batch_launch, rmat_batch_
 LAUNCH_SHAPES = [(1024, 1, 512), (1024, 1, 256), (768, 1, 512), (512, 2, 512), (512, 1, 1024), (256, 4, 512)]
 BOUNDS = [1 << b for b in range(8, 15)]
 ELLS = [4, 5, 6, 7, 8]
+# Shared memory the batched kernel keeps ahead of its staged table (its
+# mbarrier, the current work unit and the job's 20 Philox round keys); the
+# library's kBatchHeaderBytes.
+BATCH_HEADER_BYTES = 96
 _lock = threading.Lock()
 
 
@@ -187,8 +191,7 @@ def batch_blob_budget(threads: int = 1024, tile: int = 512, u64: bool = False) -
     import torch
     smem = torch.cuda.get_device_properties(torch.cuda.current_device()).shared_memory_per_block_optin
     per_warp = tile * (16 if u64 else 8) + 3 * tile
-    header = 96  # the kernel's mbarrier, current work unit and the job's 20 Philox round keys
-    return smem - header - (threads // 32) * per_warp
+    return smem - BATCH_HEADER_BYTES - (threads // 32) * per_warp
 
 
 def plan_batch(graphs, representative=None, sample_edges: int = 1 << 24):

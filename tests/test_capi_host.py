@@ -300,3 +300,12 @@ def test_dedup_host_checks():
 def test_selftest_argument_check():
     with pytest.raises(rm.RmatError):
         rm.rmat_selftest_bounded_wait(0)
+
+
+def test_batch_header_size_matches_the_library():
+    """The autotuner's shared-memory budget for batched tables subtracts the
+    same header as the batched kernel lays out."""
+    from paper_1905_03525_gb300 import autotune
+    src = open(os.path.join(ROOT, "paper_1905_03525_gb300", "csrc", "rmat_kernels.h")).read()
+    m = re.search(r"constexpr size_t kBatchHeaderBytes = (\d+);", src)
+    assert m and int(m.group(1)) == autotune.BATCH_HEADER_BYTES

@@ -309,3 +309,44 @@ def test_batch_header_size_matches_the_library():
     src = open(os.path.join(ROOT, "paper_1905_03525_gb300", "csrc", "rmat_kernels.h")).read()
     m = re.search(r"constexpr size_t kBatchHeaderBytes = (\d+);", src)
     assert m and int(m.group(1)) == autotune.BATCH_HEADER_BYTES
+
+
+def _prototypes():
+    """(name, [parameter declarations]) of every function in include/*.h."""
+    out = {}
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", fn)).read(), flags=re.S)
+        for m in re.finditer(r"(rmat_[A-Za-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S):
+            params = [p.strip() for p in m.group(2).split(",")]
+            out[m.group(1)] = [] if params == ["void"] or params == [""] else params
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    """Every prototype's parameters have the ctypes types the binding declares
+    (pointer and handle -> void*, double, int, unsigned / uint32_t, uint64_t)."""
+    c = ctypes
+
+    def kind(decl):
+        if "*" in decl or decl.startswith("rmat_stream_t"):
+            return c.c_void_p
+        t = decl.replace("const ", "").split()[0]
+        return {"double": c.c_double, "int": c.c_int, "unsigned": c.c_uint, "uint32_t": c.c_uint,
+                "uint64_t": c.c_uint64}.get(t)
+
+    protos = _prototypes()
+    sigs = {name: args for name, _, args in _capi.SIGNATURES}
+    checked = 0
+    for name, params in protos.items():
+        if name not in sigs:
+            continue
+        assert len(params) == len(sigs[name]), (name, params)
+        for decl, bound in zip(params, sigs[name]):
+            want = kind(decl)
+            if want is not None:
+                assert ctypes.sizeof(want) == ctypes.sizeof(bound) and (want is c.c_double) == (bound is c.c_double), \
+                    (name, decl, bound)
+        checked += 1
+    assert checked == len(protos) == len(declared_functions())

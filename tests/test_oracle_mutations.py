@@ -60,6 +60,13 @@ MUTATIONS = [
      [lambda: pins.test_kron_table_sizes_and_prefix_code(3, 104)]),
     ("tile prefix dropped", "        uint64_t r = pre_r, c = pre_c;", "        uint64_t r = pre_r, c = 0;",
      [pins.test_partitioned_graph_has_the_kronecker_distribution]),
+    ("per-level groups drawn in reverse order", "const orc_table *t = tables[ngroups > 1 ? n : 0];",
+     "const orc_table *t = tables[ngroups > 1 ? (uint64_t)ngroups - 1 - n : 0];",
+     [lambda: pins.test_per_level_generation_follows_each_levels_parameters(2)]),
+    ("Kronecker truncation keeps the bottom digits",
+     "                int s = t->sym[(size_t)sel * KRON_MAX_DEPTH + lvl];\n                r = r * n0 + (uint64_t)(s / t->n0);",
+     "                int s = t->sym[(size_t)sel * KRON_MAX_DEPTH + (L - take) + lvl];\n                r = r * n0 + (uint64_t)(s / t->n0);",
+     [pins.test_kron_generated_edges_follow_kronecker_power]),
     ("edge numbering restarts in every tile", "x->first[x->n] = x->next;", "x->first[x->n] = 0;",
      [pins.test_tile_counts_expectation_and_numbering]),
 ]

@@ -296,6 +296,25 @@ def test_per_level_quadrant_frequencies(sampler):
         assert abs(counts[t][[1, 3]].sum() / m - (ASYM[1] + ASYM[3])) < 5 * math.sqrt(0.25 / m)
 
 
+@pytest.mark.parametrize("ell", [2, 3])
+def test_per_level_generation_follows_each_levels_parameters(ell):
+    """Per-level tables (one fixed-l table per group of l levels): generated
+    edges take level t's quadrant with level t's own parameters, and the
+    joint law of all k = 6 levels is their Kronecker product."""
+    k, m = 6, 1 << 19
+    P = np.random.default_rng(40 + ell).dirichlet([6, 3, 2, 1], size=k)
+    row, col = oracle.generate(oracle.level_groups(P, k, ell), k, 21, 0, m)
+    counts = _quadrant_counts(row, col, k)
+    for t in range(k):
+        assert _chi2_pvalue(counts[t], P[t]) > 1e-3, t
+    joint = np.bincount(row.astype(np.int64) * (1 << k) + col.astype(np.int64), minlength=1 << (2 * k)).astype(float)
+    probs = kronecker(P, k).ravel()
+    small = probs * m < 5  # cells expecting fewer than 5 edges are pooled into one
+    cc = np.concatenate([[joint[small].sum()], joint[~small]])
+    pp = np.concatenate([[probs[small].sum()], probs[~small]])
+    assert _chi2_pvalue(cc, pp) > 1e-3
+
+
 def test_full_joint_distribution_k6():
     k, m = 6, 1 << 20
     t = oracle.Table.variable(*ASYM, k, 700)

@@ -28,6 +28,10 @@
  *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key = seed
  *     and counter = (block q, edge index e); edge e consumes words 0, 1, 2,
  *     ... of its own stream, one 32-bit word per alias draw.
+ *   - Sizes: one call generates at most RMAT_MAX_EDGES edges (per graph of a
+ *     batch, per request of a server, per partitioned graph); larger counts
+ *     return RMAT_ERR_INVALID_ARGUMENT.  edge_offset + count must also fit
+ *     64 bits.
  */
 #ifndef RMAT_H
 #define RMAT_H
@@ -51,6 +55,9 @@ typedef enum {
 } rmat_status;
 
 typedef struct rmat_table rmat_table; /* opaque; owned by the library */
+
+/* Largest edge count of one call (2^56: 2^60 bytes of u64 output). */
+#define RMAT_MAX_EDGES (1ull << 56)
 
 /* Table flags. */
 #define RMAT_UNDIRECTED 1u /* emit (min(r,c), max(r,c)): mirror the lower-left triangle (Sec. 3) */
@@ -452,9 +459,14 @@ void rmat_server_destroy(rmat_server *s);
  *     one 4-byte entry per work unit (262144 edges; 131072 for k > 32 or
  *     when a table is too large for the default tile) must fit the scratch.
  *     Anything larger returns RMAT_ERR_INVALID_ARGUMENT and launches nothing.
- *   - The first call on a device looks up the scratch's device address (once
- *     per device, with that device current); make that first call before any
- *     stream capture.
+ *   - Set-up: the first call on a device looks up the scratch's device
+ *     address (once per device, with that device current) and loads the
+ *     batched kernel there.  The runtime may defer placing the scratch (and
+ *     the kernel code) in device memory until this first use, so that first
+ *     call can take device memory.  A call with n = 0 does exactly this set-up
+ *     and launches nothing (the argument arrays may then be NULL): make it on
+ *     each device before reserving the rest of the device's memory, and before
+ *     any stream capture; later calls then take no device memory at all.
  *   - Asynchronous on `stream`.  Every call shares the one scratch array and
  *     overwrites it (the work counter is cleared each call): calls whose work
  *     overlaps on the GPU -- on different streams, or from threads that race

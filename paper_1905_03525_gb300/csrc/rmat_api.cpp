@@ -77,10 +77,9 @@ rmat_status check_generate_args(const rmat_table *t, uint64_t edge_offset, uint6
     if (!t) return fail(RMAT_ERR_INVALID_ARGUMENT, "table is NULL");
     if (count && !out) return fail(RMAT_ERR_INVALID_ARGUMENT, "output pointer is NULL");
     if (reinterpret_cast<uintptr_t>(out) & 7u) return fail(RMAT_ERR_INVALID_ARGUMENT, "output must be 8-byte aligned");
+    if (count > RMAT_MAX_EDGES) return fail(RMAT_ERR_INVALID_ARGUMENT, "count above RMAT_MAX_EDGES");
     if (count > ~uint64_t(0) - edge_offset)
         return fail(RMAT_ERR_INVALID_ARGUMENT, "edge_offset + count overflows 64 bits");
-    const uint64_t eb = wide_ids(t) ? 16 : 8;
-    if (count > (~uint64_t(0)) / eb) return fail(RMAT_ERR_INVALID_ARGUMENT, "count too large");
     return RMAT_OK;
 }
 
@@ -471,6 +470,7 @@ rmat_status rmat_generate_naive(const double *abcd, int k, unsigned flags, uint6
     if (flags & ~RMAT_UNDIRECTED) return fail(RMAT_ERR_INVALID_ARGUMENT, "unknown flag");
     if (count && !out) return fail(RMAT_ERR_INVALID_ARGUMENT, "output pointer is NULL");
     if (reinterpret_cast<uintptr_t>(out) & 7u) return fail(RMAT_ERR_INVALID_ARGUMENT, "output must be 8-byte aligned");
+    if (count > RMAT_MAX_EDGES) return fail(RMAT_ERR_INVALID_ARGUMENT, "count above RMAT_MAX_EDGES");
     if (count > ~uint64_t(0) - edge_offset)
         return fail(RMAT_ERR_INVALID_ARGUMENT, "edge_offset + count overflows 64 bits");
     std::vector<uint32_t> thr(size_t(3) * k);

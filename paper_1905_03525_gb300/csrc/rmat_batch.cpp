@@ -200,6 +200,7 @@ rmat_status rmat_batch_add(rmat_batch *b, const rmat_table *t, uint64_t seed, ui
     if (t->n0 > 2) return fail(RMAT_ERR_UNSUPPORTED, "Kronecker tables (n0 > 2) are generated by rmat_generate only");
     if (count && !out) return fail(RMAT_ERR_INVALID_ARGUMENT, "output pointer is NULL");
     if (reinterpret_cast<uintptr_t>(out) & 7u) return fail(RMAT_ERR_INVALID_ARGUMENT, "output must be 8-byte aligned");
+    if (count > RMAT_MAX_EDGES) return fail(RMAT_ERR_INVALID_ARGUMENT, "count above RMAT_MAX_EDGES");
     if (count > ~uint64_t(0) - edge_offset)
         return fail(RMAT_ERR_INVALID_ARGUMENT, "edge_offset + count overflows 64 bits");
     if (b->entries.size() >= 0xFFFFFFFFu) return fail(RMAT_ERR_INVALID_ARGUMENT, "too many graphs");

@@ -206,6 +206,7 @@ rmat_status rmat_partition_create(const rmat_table *t, int tile_levels, uint64_t
         return fail(RMAT_ERR_INVALID_ARGUMENT, "tile_levels must be in [0, min(k, 30)]");
     if (row_tile_begin > row_tile_end || row_tile_end > (uint64_t(1) << tile_levels))
         return fail(RMAT_ERR_INVALID_ARGUMENT, "tile rows must satisfy begin <= end <= 2^tile_levels");
+    if (m > RMAT_MAX_EDGES) return fail(RMAT_ERR_INVALID_ARGUMENT, "m above RMAT_MAX_EDGES");
     rmat_partition *p = new (std::nothrow) rmat_partition;
     if (!p) return fail(RMAT_ERR_OUT_OF_MEMORY, "host allocation failed");
     p->t = t;

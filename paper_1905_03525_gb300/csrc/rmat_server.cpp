@@ -442,6 +442,7 @@ rmat_status rmat_server_submit(rmat_server *s, const rmat_request_t *req, uint64
     clear_error();
     if (!s || !req) return fail(RMAT_ERR_INVALID_ARGUMENT, "NULL argument");
     if (req->m == 0) return fail(RMAT_ERR_INVALID_ARGUMENT, "a request needs m >= 1 edges");
+    if (req->m > RMAT_MAX_EDGES) return fail(RMAT_ERR_INVALID_ARGUMENT, "m above RMAT_MAX_EDGES");
     // table_bound 0: the largest power-of-two bound <= 8192 whose blob the
     // batched kernel can stage in shared memory (deep paths of skewed
     // parameters make wide, 36-byte columns); otherwise exactly the bound asked.

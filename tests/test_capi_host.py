@@ -132,6 +132,39 @@ def test_generate_argument_checks_need_no_device():
     rm.rmat_generate(t, 1, 0, 0, 0)               # count == 0 is a no-op
 
 
+MAX_EDGES = 1 << 56   # RMAT_MAX_EDGES of include/rmat.h
+
+
+def test_counts_near_2p64_are_rejected_on_host():
+    """Counts whose ceiling divisions by a tile or a work unit would wrap
+    (2^64 - 1 edges from offset 0) stop at the per-call maximum, before any
+    device work; the maximum itself passes the host checks."""
+    t = rm.rmat_build_table(*G500, 26, 4096)
+    for count in ((1 << 64) - 1, (1 << 64) - 512, MAX_EDGES + 1):
+        with pytest.raises(rm.RmatError) as ei:
+            rm.rmat_generate(t, 1, 0, count, 0x1000)
+        assert ei.value.status == _capi.RMAT_ERR_INVALID_ARGUMENT and "RMAT_MAX_EDGES" in ei.value.message
+        with pytest.raises(rm.RmatError) as ei:
+            rm.rmat_generate_host(t, 1, 0, count, 0x1000)
+        assert "RMAT_MAX_EDGES" in ei.value.message
+        with pytest.raises(rm.RmatError) as ei:
+            rm.rmat_generate_naive(G500, 26, 0, 1, 0, count, 0x1000)
+        assert "RMAT_MAX_EDGES" in ei.value.message
+        b = rm.rmat_batch_create()
+        with pytest.raises(rm.RmatError) as ei:
+            rm.rmat_batch_add(b, t, 1, 0, count, 0x1000)
+        assert "RMAT_MAX_EDGES" in ei.value.message
+        with pytest.raises(rm.RmatError) as ei:
+            rm.rmat_partition_create(t, 2, count, 1)
+        assert "RMAT_MAX_EDGES" in ei.value.message
+        with pytest.raises(rm.RmatError) as ei:
+            rm.rmat_generate_batch_noalloc([t], [1], [0], [count], [0x1000])
+        assert "RMAT_MAX_EDGES" in ei.value.message
+    b = rm.rmat_batch_create()
+    rm.rmat_batch_add(b, t, 1, 0, MAX_EDGES, 0x1000)
+    assert rm.rmat_batch_size(b) == (1, MAX_EDGES)
+
+
 def test_batch_host_checks():
     b = rm.rmat_batch_create()
     t = rm.rmat_build_table(*G500, 20, 1000)

@@ -1058,6 +1058,18 @@ rmat_status batch_occupancy(bool u64, int threads, size_t smem, int &per_sm) {
     return RMAT_OK;
 }
 
+rmat_status load_batch_kernels() {
+    for (bool u64 : {false, true})
+        for (bool general : {false, true}) {
+            cudaFuncAttributes attr;
+            cudaError_t e = cudaFuncGetAttributes(&attr, batch_kernel(u64, general));
+            if (e == cudaSuccess) e = set_smem_attr(batch_kernel(u64, general), 0);
+            if (e != cudaSuccess)
+                return fail(RMAT_ERR_CUDA, std::string("loading the batched kernel: ") + cudaGetErrorString(e));
+        }
+    return RMAT_OK;
+}
+
 rmat_status launch_batch(bool u64, const BatchArgs &args, int grid, int threads, size_t smem, cudaStream_t stream) {
     void *fn = batch_kernel(u64, args.general != 0);
     cudaError_t e = cudaMemsetAsync(args.counter, 0, sizeof(unsigned long long), stream);

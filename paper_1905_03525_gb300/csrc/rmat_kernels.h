@@ -102,6 +102,9 @@ size_t warp_bytes(bool u64, bool levels, int tile);
 size_t batch_smem_bytes(bool u64, int threads, int tile, uint32_t max_blob_bytes);
 rmat_status batch_occupancy(bool u64, int threads, size_t smem, int &per_sm);
 rmat_status launch_batch(bool u64, const BatchArgs &args, int grid, int threads, size_t smem, cudaStream_t stream);
+// Load every variant of the batched kernel on the current device now (code
+// and attributes), so that no later launch has module loading to do.
+rmat_status load_batch_kernels();
 rmat_status launch_checksum(bool u64, const BatchArgs &args, unsigned long long *sums, int grid,
                             cudaStream_t stream);
 rmat_status launch_naive(const uint32_t *thr3, int k, unsigned flags, uint64_t seed, uint64_t e0,

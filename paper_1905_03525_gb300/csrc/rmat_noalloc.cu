@@ -31,11 +31,15 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[RMAT_NOALLOC_SC
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char *g_scratch_ptr[kMaxDevices] = {};  // device address of the scratch, per device
+bool g_kernels_loaded[kMaxDevices] = {};           // batched kernel loaded on the device
 
 // Host staging of one call's scratch image (static: the call allocates
 // nothing; the mutex serialises calls on the host).
 unsigned char g_host_image[RMAT_NOALLOC_SCRATCH_BYTES];
 
+// Device address of the scratch on device `dev` (current), looked up once per
+// device; the first lookup also loads the batched kernel there.  Called with
+// g_mu held.
 rmat_status scratch_address(int dev, unsigned char **out) {
     if (dev < 0 || dev >= kMaxDevices) return fail(RMAT_ERR_UNSUPPORTED, "device ordinal out of range");
     if (!g_scratch_ptr[dev]) {
@@ -46,6 +50,10 @@ rmat_status scratch_address(int dev, unsigned char **out) {
         g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
     }
     *out = g_scratch_ptr[dev];
+    if (!g_kernels_loaded[dev]) {
+        if (rmat_status st = load_batch_kernels()) return st;
+        g_kernels_loaded[dev] = true;
+    }
     return RMAT_OK;
 }
 
@@ -60,7 +68,19 @@ extern "C" rmat_status rmat_generate_batch_noalloc(const rmat_table *const *tabl
                                                    const uint64_t *edge_offsets, const uint64_t *counts,
                                                    void *const *outs, uint32_t n, rmat_stream_t stream_) {
     clear_error();
-    if (n == 0) return RMAT_OK;
+    if (n == 0) {
+        // Set-up only: the scratch's device address (loading its module) and
+        // the batched kernel's code on this device, so that later calls find
+        // everything resident -- nothing is launched.
+        int dev = 0;
+        const cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+        DeviceProps props;
+        if (rmat_status st = device_props(props)) return st;
+        std::lock_guard<std::mutex> lk(g_mu);
+        unsigned char *scratch = nullptr;
+        return scratch_address(dev, &scratch);
+    }
     if (!tables || !seeds || !edge_offsets || !counts || !outs)
         return fail(RMAT_ERR_INVALID_ARGUMENT, "NULL argument array");
     if (n > RMAT_NOALLOC_MAX_GRAPHS)
@@ -73,6 +93,7 @@ extern "C" rmat_status rmat_generate_batch_noalloc(const rmat_table *const *tabl
         if (counts[i] && !outs[i]) return fail(RMAT_ERR_INVALID_ARGUMENT, "NULL output pointer");
         if (reinterpret_cast<uintptr_t>(outs[i]) & 7u)
             return fail(RMAT_ERR_INVALID_ARGUMENT, "output must be 8-byte aligned");
+        if (counts[i] > RMAT_MAX_EDGES) return fail(RMAT_ERR_INVALID_ARGUMENT, "count above RMAT_MAX_EDGES");
         if (counts[i] > ~uint64_t(0) - edge_offsets[i])
             return fail(RMAT_ERR_INVALID_ARGUMENT, "edge_offset + count overflows 64 bits");
         if (i == 0) u64 = tables[0]->k > 32;
@@ -149,8 +170,11 @@ extern "C" rmat_status rmat_generate_batch_noalloc(const rmat_table *const *tabl
         std::memcpy(g_host_image + blob_off[i], t->image.data(), t->image.size() * 4);
     }
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-    // Pageable source: the call returns once the bytes are staged, so the
-    // static host image can be reused by the next call.
+    // Pageable source: for a host-to-device copy from pageable memory the
+    // runtime copies the source into its own staging memory before
+    // cudaMemcpyAsync returns (CUDA Runtime API, "API synchronization
+    // behavior"), so the next call may rewrite the static host image while
+    // this copy is still queued on the stream.
     e = cudaMemcpyAsync(scratch, g_host_image, end, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("scratch upload: ") + cudaGetErrorString(e));
     if (units == 0) return RMAT_OK;

@@ -193,6 +193,37 @@ def generate(tables, k, seed, e0, count, undirected=False):
     return row, col
 
 
+def generate_parallel(tables, k, seed, e0, count, undirected=False, threads=None):
+    """generate() split over host threads, each taking one consecutive run of
+    the edge range.  Edge e depends only on the tables, the seed and e (the
+    counter-based stream), so the split changes nothing but the wall time."""
+    tables = list(tables)
+    threads = max(1, min(threads or os.cpu_count() or 1, count // 4096 or 1))
+    row = np.zeros(count, np.uint64)
+    col = np.zeros(count, np.uint64)
+    h = _handles(tables)
+    per = (count + threads - 1) // threads
+    rcs = [0] * threads
+
+    def work(i):
+        lo = i * per
+        n = max(0, min(count, lo + per) - lo)
+        if n:
+            rcs[i] = lib().orc_generate(h, len(tables), k, int(undirected), seed, e0 + lo, n,
+                                        row[lo:].ctypes.data_as(ctypes.c_void_p),
+                                        col[lo:].ctypes.data_as(ctypes.c_void_p))
+
+    lib()
+    ts = [threading.Thread(target=work, args=(i,)) for i in range(threads)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    if any(rcs):
+        raise ValueError("oracle rejected the generate arguments")
+    return row, col
+
+
 def scramble_constants(scramble_seed: int, k: int) -> np.ndarray:
     out = np.zeros(6, np.uint64)
     lib().orc_scramble_constants(scramble_seed, k, _ptr(out))

@@ -166,22 +166,35 @@ def tune_levels(k: int, P_levels, flags: int = 0, sample_edges: int = 1 << 24, e
     return best
 
 
-def build_tuned_table(k: int, abcd, m: int | None = None, choice=None):
-    """Build the table the tuner picked for (k, params).  For a graph of m
-    edges the table's blob is also kept below 1/8 of the graph's output bytes
-    (staging a table costs about its own size in traffic per CTA)."""
-    choice = choice or tune_table(k, abcd)
+def tuned_table_spec(k: int, choice, m: int | None = None):
+    """("variable", bound) or ("fixed", l): the table build_tuned_table makes
+    for (k, choice) and a graph of m edges.  For a graph of m edges the table's
+    blob is also kept below 1/8 of the graph's output bytes (staging a table
+    costs about its own size in traffic per CTA)."""
     if choice["kind"] == "fixed":
         ell = min(choice["ell"], k)
         if m is not None:
             while ell > 2 and 8 * 4 ** ell > m:   # table bytes <= 1/8 of the output bytes
                 ell -= 1
-        return rmat_build_table_fixed(*abcd, k, ell)
+        return ("fixed", ell)
     bound = choice["bound"]
     if m is not None:
         while bound > 64 and 8 * bound > m:
             bound //= 2
-    return rmat_build_table(*abcd, k, bound)
+    return ("variable", bound)
+
+
+def build_tuned_table(k: int, abcd, m: int | None = None, choice=None):
+    """Build the table the tuner picked for (k, params), sized for m edges
+    (tuned_table_spec); the returned table carries its spec as `.spec`."""
+    choice = choice or tune_table(k, abcd)
+    spec = tuned_table_spec(k, choice, m)
+    if spec[0] == "fixed":
+        t = rmat_build_table_fixed(*abcd, k, spec[1])
+    else:
+        t = rmat_build_table(*abcd, k, spec[1])
+    t.spec = spec
+    return t
 
 
 def batch_blob_budget(threads: int = 1024, tile: int = 512, u64: bool = False) -> int:

@@ -1,10 +1,8 @@
 """GPU parity: librmat's kernels against the CPU oracle, bit for bit.
 
 Every case runs through the C ABI (the ctypes binding) on seeded synthetic
-inputs.  Small cases compare every edge; the full-size cases (the 2^30-edge
-k = 26 workload in the benchmark's launch shape, and one 2^30-edge chunk of
-the k = 34 per-level workload) compare sampled runs of edges that the oracle
-recomputes one by one, plus whole-output properties.
+inputs and compares every edge; the full-size workloads are compared edge
+for edge in test_gpu_fullsize.py.
 """
 import numpy as np
 import pytest
@@ -172,61 +170,6 @@ def test_streams_are_honoured():
         rm.rmat_generate(t, 1, 0, m, out, s)
     s.synchronize()
     assert_same(as_u64_pairs(out[:4096], k), oracle.generate([oracle.Table.variable(*G500, k, 4096)], k, 1, 0, 4096))
-
-
-# --------------------------------------------------------- full-size cases --
-
-def _sample_ranges(m, rng, n=24, width=2048):
-    starts = {0, m - width}
-    while len(starts) < n:
-        starts.add(int(rng.integers(0, m - width)))
-    return sorted(starts)
-
-
-def test_k26_full_size_in_bench_shape():
-    """k = 26, m = 2^30 (edge factor 16), variable table bound 2^12: the
-    benchmark's workload and launch shape.  Sampled edges are recomputed by the
-    oracle; whole-output marginals must match the Kronecker closed form."""
-    k, m = 26, 1 << 30
-    t = rm.rmat_build_table(*G500, k, 4096)
-    ot = oracle.Table.variable(*G500, k, 4096)
-    out = rm.empty_edges(m, k)
-    rm.rmat_generate(t, 1, 0, m, out)
-    torch.cuda.synchronize()
-    rng = np.random.default_rng(26)
-    for s in _sample_ranges(m, rng):
-        assert_same(as_u64_pairs(out[s:s + 2048], k), oracle.generate([ot], k, 1, s, 2048))
-    # property at full size: the top-level quadrant frequencies
-    rows = out[:, 0].view(torch.int32)
-    cols = out[:, 1].view(torch.int32)
-    top_r = ((rows >> (k - 1)) & 1).to(torch.int64)
-    top_c = ((cols >> (k - 1)) & 1).to(torch.int64)
-    counts = torch.bincount(2 * top_r + top_c, minlength=4).cpu().numpy().astype(float)
-    p = np.array(G500) / sum(G500)
-    z = (counts - p * m) / np.sqrt(m * p * (1 - p))
-    assert np.all(np.abs(z) < 6), z
-    del out
-    torch.cuda.empty_cache()
-
-
-def test_k34_per_level_chunk_full_size():
-    """One 2^30-edge chunk (edges 31 * 2^30 ..) of the k = 34, per-level noisy,
-    undirected, u64 workload; sampled edges against the oracle."""
-    k, m, ell = 34, 1 << 30, 6
-    P = noisy_levels(k)
-    t = rm.rmat_build_table_levels(P, k, ell, rm.RMAT_UNDIRECTED)
-    groups = oracle.level_groups(P, k, ell)
-    e0 = 31 << 30
-    out = rm.empty_edges(m, k)
-    rm.rmat_generate(t, 34, e0, m, out)
-    torch.cuda.synchronize()
-    rng = np.random.default_rng(34)
-    for s in _sample_ranges(m, rng, n=16, width=1024):
-        ref = oracle.generate(groups, k, 34, e0 + s, 1024, undirected=True)
-        assert_same(as_u64_pairs(out[s:s + 1024], k), ref)
-    assert bool((out[:, 0] <= out[:, 1]).all())
-    del out
-    torch.cuda.empty_cache()
 
 
 def test_tables_with_different_shared_memory_needs_interleave():

@@ -1,7 +1,8 @@
 """Serving with continuous batching: every request's result is the same
-alone and in the mix (checksums against the single-graph entry point, and
-full chunk bytes seen through the callback), admission backs off on memory,
-and host-side waits time out without disturbing the server."""
+alone and in the mix -- checksums and full chunk bytes (seen through the
+callback) against the CPU oracle and against the single-graph entry point --
+admission backs off on memory, and host-side waits time out without
+disturbing the server."""
 import ctypes
 import ctypes.util
 import os
@@ -9,6 +10,7 @@ import os
 import numpy as np
 import pytest
 
+import oracle
 import paper_1905_03525_gb300 as rm
 from paper_1905_03525_gb300 import _capi
 from paper_1905_03525_gb300.serve import DONE, Server
@@ -45,6 +47,14 @@ def alone(abcd, k, m, seed, bound=4096):
     return h[:, 0].astype(np.uint64), h[:, 1].astype(np.uint64)
 
 
+def oracle_edges(abcd, k, m, seed, bound, undirected=False, scramble_seed=None):
+    """The request's edges from the CPU oracle (table of the bound the server used)."""
+    t = [oracle.Table.variable(*abcd, k, bound)]
+    if scramble_seed is not None:
+        return oracle.generate_scrambled(t, k, scramble_seed, seed, 0, m, undirected=undirected)
+    return oracle.generate_parallel(t, k, seed, 0, m, undirected=undirected)
+
+
 REQS = [(G500, 20, 100_000, 1), (SKEWED, 26, 300_001, 2), ((0.5, 0.2, 0.25, 0.05), 12, 5_000, 3),
         (G500, 30, 1 << 19, 4), (G500, 16, 70_000, 5), ((0.45, 0.22, 0.22, 0.11), 24, 250_000, 6),
         (G500, 34, 40_000, 7), (G500, 8, 1, 8), (SKEWED, 18, 200_000, 9), (G500, 22, 65_536, 10)]
@@ -66,8 +76,10 @@ def test_results_same_alone_and_in_the_mix():
     assert all(x["state"] == DONE and x["edges_done"] == m for x, (_, _, m, _) in zip(mixed, REQS))
     assert st["steps"] > len(REQS)  # multi-chunk requests really were split
     for x, (p, k, m, s) in zip(mixed, REQS):
+        r, c = oracle_edges(p, k, m, s, x["table_bound"])
+        assert x["checksum"] == host_checksum(r, c, 0), ("oracle", k, m)
         r, c = alone(p, k, m, s, x["table_bound"])
-        assert x["checksum"] == host_checksum(r, c, 0), (k, m)
+        assert x["checksum"] == host_checksum(r, c, 0), ("alone", k, m)
     # auto bounds: deep (wide-entry) tables were shrunk to fit shared memory
     assert mixed[1]["table_bound"] < mixed[0]["table_bound"] <= 8192
     # one request alone on its own server gives the same checksum
@@ -117,6 +129,44 @@ def test_chunk_callback_sees_every_edge():
         data = data.view(np.uint32 if k <= 32 else np.uint64).reshape(-1, 2)
         r, c = alone(p, k, m, s, bounds[rid])
         assert np.array_equal(data[:, 0].astype(np.uint64), r) and np.array_equal(data[:, 1].astype(np.uint64), c)
+
+
+def test_served_bytes_match_oracle():
+    """One request of each kind -- u32, u64 IDs, undirected, scrambled, and a
+    skewed deep table -- served together with the server's own table bounds;
+    every byte seen by the callback and every checksum against the oracle."""
+    rt = _cudart()
+    rt.cudaMemcpy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+    got = {}
+
+    def on_chunk(rid, off, cnt, ptr):
+        eb = got[rid]["eb"]
+        buf = np.empty(cnt * eb // 4, np.uint32)
+        assert rt.cudaMemcpy(buf.ctypes.data, ptr, cnt * eb, 2) == 0
+        got[rid]["parts"].append((off, buf))
+
+    # (params, k, m, seed, flags, scramble seed)
+    reqs = [(G500, 24, 300_007, 21, 0, None), (G500, 44, 120_001, 22, 0, None),
+            (SKEWED, 30, 200_003, 23, rm.RMAT_UNDIRECTED, None), ((0.45, 0.22, 0.22, 0.11), 28, 150_000, 24, 0, 99),
+            (G500, 36, 90_000, 25, rm.RMAT_UNDIRECTED, 7), (SKEWED, 26, 250_000, 26, 0, None)]
+    with Server(256 << 20, chunk_edges=1 << 15, step_edges=1 << 17, max_active=3) as srv:
+        srv.set_chunk_callback(on_chunk)
+        for p, k, m, s, fl, scr in reqs:
+            rid = srv.submit(*p, k, m, s, flags=fl, scramble_seed=scr)
+            got[rid] = {"eb": 8 if k <= 32 else 16, "parts": [], "req": (p, k, m, s, fl, scr)}
+        srv.drain(600)
+        status = {rid: srv.status(rid) for rid in got}
+    for rid, g in got.items():
+        p, k, m, s, fl, scr = g["req"]
+        st = status[rid]
+        assert st["state"] == DONE and st["edges_done"] == m
+        parts = sorted(g["parts"], key=lambda x: x[0])
+        assert [o for o, _ in parts] == list(range(0, m, 1 << 15))
+        data = np.concatenate([b for _, b in parts]).view(np.uint32 if k <= 32 else np.uint64).reshape(-1, 2)
+        r, c = oracle_edges(p, k, m, s, st["table_bound"], undirected=bool(fl), scramble_seed=scr)
+        bad = np.nonzero((data[:, 0] != r) | (data[:, 1] != c))[0]
+        assert bad.size == 0, (k, fl, scr, st["table_bound"], bad[:5])
+        assert st["checksum"] == host_checksum(r, c, 0), (k, fl, scr)
 
 
 def test_admission_backs_off_on_memory():

@@ -138,12 +138,13 @@ __device__ __forceinline__ uint4 philox_sks(uint32_t c0, uint32_t c1, uint32_t c
     return make_uint4(c0, c1, c2, c3);
 }
 
-// Where one table (group) lives and how to split a word for it.
+// Where one table (group) lives and how to split a word for it.  Every table
+// has b >= 2 (at least four entries), so the column shift is 2..30.
 template <bool SMEM>
 struct Group {
     uint32_t sA, sBs, sBa;            // shared byte addresses (SMEM)
     const uint32_t *gA, *gBs, *gBa;   // global addresses (!SMEM)
-    uint32_t mulb;                    // 2^b: column j = umulhi(u, 2^b)
+    uint32_t shb;                     // 32 - b: column j = u >> (32 - b)
 };
 
 // Blob header word `w` (group descriptors), from shared or global memory.
@@ -166,7 +167,7 @@ __device__ __forceinline__ Group<SMEM> group(uint32_t sbase, const uint32_t *gbl
     G.gA = gblob + aoff;
     G.gBs = gblob + bsoff;
     G.gBa = gblob + baoff;
-    G.mulb = 1u << bits;
+    G.shb = 32u - bits;
     return G;
 }
 
@@ -176,6 +177,12 @@ __device__ __forceinline__ Group<SMEM> group(uint32_t sbase, const uint32_t *gbl
 struct Acc32 {
     uint32_t row, col, filled;
     __device__ __forceinline__ void clear() { row = col = filled = 0; }
+    // The first path of an edge: nothing to shift.
+    __device__ __forceinline__ void set(uint32_t r, uint32_t c, uint32_t L) {
+        row = r;
+        col = c;
+        filled = L;
+    }
     // Any number of levels may be appended: shifts of 32 or more give 0.
     __device__ __forceinline__ void append(uint32_t r, uint32_t c, uint32_t L) {
         row |= shr_clamp(r, filled);
@@ -190,6 +197,11 @@ struct Acc64 {
     uint64_t row, col;
     uint32_t filled;
     __device__ __forceinline__ void clear() { row = col = 0; filled = 0; }
+    __device__ __forceinline__ void set(uint32_t r, uint32_t c, uint32_t L) {
+        row = uint64_t(r) << 32;
+        col = uint64_t(c) << 32;
+        filled = L;
+    }
     // Only called while filled < k <= 64.
     __device__ __forceinline__ void append(uint32_t r, uint32_t c, uint32_t L) {
         row |= (uint64_t(r) << 32) >> filled;
@@ -200,35 +212,47 @@ struct Acc64 {
     __device__ __forceinline__ uint64_t out_col(int k) const { return col >> (64 - k); }
 };
 
-// One alias draw from word u, appended to acc: column j = top b bits of u
-// (the high word of u * 2^b); the draw keeps j iff u < A[j] =
-// (j << (32-b)) + thr[j], i.e. iff the residual (low 32-b bits) < thr[j],
-// and then appends path Bs[j], else path Ba[j] (the alias's).
+// One alias draw from word u: column j = top b bits of u; the draw keeps j
+// iff u < A[j] = (j << (32-b)) + thr[j], i.e. iff the residual (low 32-b
+// bits) < thr[j], and then takes path Bs[j], else path Ba[j] (the alias's).
 // Compact path entry x: row bits in 31..19, length in 18..13, column bits in
-// 12..0 (both left-aligned in their 13-bit fields).
-template <int FMT, bool SMEM, class Acc>
+// 12..0 (both left-aligned in their 13-bit fields); wide entry: {row, col,
+// length, 0}.  `first` sets the accumulators (an edge's first path needs no
+// shift), otherwise the path is appended.
+template <int FMT, bool SMEM, bool FIRST = false, class Acc>
 __device__ __forceinline__ void draw(const Group<SMEM> &G, uint32_t u, Acc &acc) {
-    const uint32_t j = __umulhi(u, G.mulb);
+    const uint32_t j = u >> G.shb;
+    uint32_t r, c, L;
     if constexpr (SMEM) {
         const uint32_t off = 4u * j;
         const bool keep = u < lds32(G.sA + off);
         if constexpr (FMT == 0) {
             const uint32_t x = lds32((keep ? G.sBs : G.sBa) + off);
-            acc.append(x & 0xFFF80000u, x << 19, (x >> 13) & 63u);
+            r = x & 0xFFF80000u;
+            c = x << 19;
+            L = (x >> 13) & 63u;
         } else {
             const uint4 v = lds128((keep ? G.sBs : G.sBa) + 4u * off);
-            acc.append(v.x, v.y, v.z);
+            r = v.x;
+            c = v.y;
+            L = v.z;
         }
     } else {
         const bool keep = u < __ldg(G.gA + j);
         if constexpr (FMT == 0) {
             const uint32_t x = __ldg((keep ? G.gBs : G.gBa) + j);
-            acc.append(x & 0xFFF80000u, x << 19, (x >> 13) & 63u);
+            r = x & 0xFFF80000u;
+            c = x << 19;
+            L = (x >> 13) & 63u;
         } else {
             const uint4 v = __ldg(reinterpret_cast<const uint4 *>(keep ? G.gBs : G.gBa) + j);
-            acc.append(v.x, v.y, v.z);
+            r = v.x;
+            c = v.y;
+            L = v.z;
         }
     }
+    if constexpr (FIRST) acc.set(r, c, L);
+    else acc.append(r, c, L);
 }
 
 // The same draw from a table of fixed-length paths (every entry has exactly
@@ -237,7 +261,7 @@ __device__ __forceinline__ void draw(const Group<SMEM> &G, uint32_t u, Acc &acc)
 template <int FMT, bool SMEM>
 __device__ __forceinline__ void draw_fixed(const Group<SMEM> &G, uint32_t u, uint32_t L, uint32_t &r,
                                            uint32_t &c) {
-    const uint32_t j = __umulhi(u, G.mulb);
+    const uint32_t j = u >> G.shb;
     const uint32_t s = 32u - L;
     if constexpr (SMEM) {
         const uint32_t off = 4u * j;

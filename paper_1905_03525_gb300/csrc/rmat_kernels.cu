@@ -73,7 +73,7 @@ __device__ __forceinline__ dev::Group<SMEM> group0(const Job &J, uint32_t sblob)
     G.gA = J.blob + J.a0;
     G.gBs = J.blob + J.bs0;
     G.gBa = J.blob + J.ba0;
-    G.mulb = 1u << J.bits0;
+    G.shb = 32u - J.bits0;
     return G;
 }
 
@@ -185,11 +185,12 @@ __device__ __forceinline__ void put_final_right(uint32_t stage, uint32_t idx, ty
 }
 
 // Phase 1 over a tile: one Philox block and up to `draws1` draws per edge,
-// several edges per lane in flight.  Finished
+// several edges per lane in flight (D = 4: draws1 is known to be 4, and the
+// four draws are straight-line code; D = 0: draws1 read from the job).  Finished
 // edges go to their output slot; unfinished ones leave their raw accumulators
 // in the same slot, their level count in p_fill, and a bit in the lane's mask
 // (bit i = edge i*32 + lane).
-template <int FMT, bool U64, bool SMEM, int EPI, bool FULL, bool PRE, class K>
+template <int FMT, bool U64, bool SMEM, int EPI, bool FULL, bool PRE, int D, class K>
 __device__ __forceinline__ uint32_t phase1(const Job &J, const K &ks, const Scramble &S,
                                            const dev::Group<SMEM> &G0, uint64_t ebase, uint32_t n, uint32_t stage,
                                            uint32_t p_fill, int lane) {
@@ -231,28 +232,30 @@ __device__ __forceinline__ uint32_t phase1(const Job &J, const K &ks, const Scra
         uint4 w[E];
         Acc a[E];
 #pragma unroll
-        for (int q = 0; q < E; ++q) {
-            w[q] = edge_block(ks, 0u, ebase + (it + q) * 32 + lane);
-            a[q].clear();
-            if constexpr (PRE) {
-                // batched jobs may start below the top level (a partition tile)
-                using Word = typename AccT<U64>::word;
+        for (int q = 0; q < E; ++q) w[q] = edge_block(ks, 0u, ebase + (it + q) * 32 + lane);
+        if constexpr (PRE) {
+            // batched jobs may start below the top level (a partition tile)
+            using Word = typename AccT<U64>::word;
+#pragma unroll
+            for (int q = 0; q < E; ++q) {
                 a[q].row = Word(J.pre_row);
                 a[q].col = Word(J.pre_col);
                 a[q].filled = J.pre_len;
+                step(a[q], w[q].x);
             }
-        }
+        } else {
 #pragma unroll
-        for (int q = 0; q < E; ++q) step(a[q], w[q].x);
-        if (J.draws1 > 1) {
+            for (int q = 0; q < E; ++q) dev::draw<FMT, SMEM, true>(G0, w[q].x, a[q]);
+        }
+        if (D >= 2 || J.draws1 > 1) {
 #pragma unroll
             for (int q = 0; q < E; ++q) step(a[q], w[q].y);
         }
-        if (J.draws1 > 2) {
+        if (D >= 3 || J.draws1 > 2) {
 #pragma unroll
             for (int q = 0; q < E; ++q) step(a[q], w[q].z);
         }
-        if (J.draws1 > 3) {
+        if (D >= 4 || J.draws1 > 3) {
 #pragma unroll
             for (int q = 0; q < E; ++q) step(a[q], w[q].w);
         }
@@ -264,11 +267,12 @@ __device__ __forceinline__ uint32_t phase1(const Job &J, const K &ks, const Scra
 }
 
 // sgroups: shared address of precomputed group descriptors (uint4 {A, Bs, Ba,
-// 2^b} per group) for per-level tables staged in shared memory, or 0 to read
+// 32 - b} per group) for per-level tables staged in shared memory, or 0 to read
 // them from the blob header at every draw.
 // ks: where the Philox round keys come from (see edge_block).  PRE: edges
-// start with the job's prefix levels (batched jobs).
-template <int FMT, bool U64, bool SMEM, bool LEVELS, int EPI, bool PRE, class K>
+// start with the job's prefix levels (batched jobs).  D: phase 1's draw count
+// when known at compile time (4), else 0.
+template <int FMT, bool U64, bool SMEM, bool LEVELS, int EPI, bool PRE, int D, class K>
 __device__ __forceinline__ void gen_tile(const Job &J, const K &ks, const Scramble &S, uint32_t sblob,
                                          const uint32_t *gblob, const dev::Group<SMEM> &G0, uint64_t first,
                                          uint32_t n, WarpState &W, uint32_t sgroups = 0) {
@@ -320,11 +324,11 @@ __device__ __forceinline__ void gen_tile(const Job &J, const K &ks, const Scramb
                             Gg.sA = gd.x;
                             Gg.sBs = gd.y;
                             Gg.sBa = gd.z;
-                            Gg.mulb = gd.w;
+                            Gg.shb = gd.w;
                         } else {
                             Gg = dev::group<SMEM>(sblob, gblob, uint32_t(g));
                         }
-                        const uint32_t L = uint32_t(31 - __clz(Gg.mulb)) >> 1;  // mulb = 2^(2 L)
+                        const uint32_t L = (32u - Gg.shb) >> 1;  // 4^L columns
 #pragma unroll
                         for (int x = 0; x < EL; ++x) {
                             uint32_t r, c;
@@ -343,8 +347,8 @@ __device__ __forceinline__ void gen_tile(const Job &J, const K &ks, const Scramb
         }
     } else {
         const uint32_t pm = n == uint32_t(W.tile)
-                                ? phase1<FMT, U64, SMEM, EPI, true, PRE>(J, ks, S, G0, ebase, n, stage, p_fill, lane)
-                                : phase1<FMT, U64, SMEM, EPI, false, PRE>(J, ks, S, G0, ebase, n, stage, p_fill, lane);
+                                ? phase1<FMT, U64, SMEM, EPI, true, PRE, D>(J, ks, S, G0, ebase, n, stage, p_fill, lane)
+                                : phase1<FMT, U64, SMEM, EPI, false, PRE, D>(J, ks, S, G0, ebase, n, stage, p_fill, lane);
         // Phase 2: queue the unfinished edges of the whole tile (warp prefix
         // sum of the lanes' counts), then finish them 32 at a time.
         const uint32_t cnt = __popc(pm);
@@ -438,7 +442,7 @@ __device__ __forceinline__ bool stage_blob(unsigned char *dst, const uint32_t *s
     return __syncthreads_and(ok) != 0;
 }
 
-template <int FMT, bool U64, bool SMEM, bool LEVELS, int EPI>
+template <int FMT, bool U64, bool SMEM, bool LEVELS, int EPI, int D>
 __global__ void __launch_bounds__(1024, 1) k_alias(const __grid_constant__ Job J, const __grid_constant__ Scramble S,
                                                 int tile, unsigned *err) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -473,7 +477,7 @@ __global__ void __launch_bounds__(1024, 1) k_alias(const __grid_constant__ Job J
         for (int g = threadIdx.x; g < J.ngroups; g += blockDim.x) {
             const dev::Group<true> Gg = dev::group<true>(sblob, J.blob, uint32_t(g));
             uint4 *d = reinterpret_cast<uint4 *>(smem + 16) + g;
-            *d = make_uint4(Gg.sA, Gg.sBs, Gg.sBa, Gg.mulb);
+            *d = make_uint4(Gg.sA, Gg.sBs, Gg.sBa, Gg.shb);
         }
         __syncthreads();
     }
@@ -489,7 +493,7 @@ __global__ void __launch_bounds__(1024, 1) k_alias(const __grid_constant__ Job J
         const uint64_t first = t * tile;
         const uint64_t left = J.count - first;
         const uint32_t n = left < uint64_t(tile) ? uint32_t(left) : uint32_t(tile);
-        gen_tile<FMT, U64, SMEM, LEVELS, EPI, false>(J, J.ks, S, sblob, J.blob, G0, first, n, W, sgroups);
+        gen_tile<FMT, U64, SMEM, LEVELS, EPI, false, D>(J, J.ks, S, sblob, J.blob, G0, first, n, W, sgroups);
     }
     if (lane == 0 && W.issued) dev::bulk_wait_all();
 }
@@ -505,7 +509,7 @@ __device__ __forceinline__ void batch_unit(const Job &J, const Scramble &S, Shar
     for (uint64_t first = f0 + uint64_t(warp) * W.tile; first < end; first += uint64_t(nwarps) * W.tile) {
         const uint64_t left = end - first;
         const uint32_t n = left < uint64_t(W.tile) ? uint32_t(left) : uint32_t(W.tile);
-        gen_tile<FMT, U64, SMEM, LEVELS, EPI, PRE>(J, ks, S, sblob, J.blob, G0, first, n, W);
+        gen_tile<FMT, U64, SMEM, LEVELS, EPI, PRE, 0>(J, ks, S, sblob, J.blob, G0, first, n, W);
     }
 }
 
@@ -754,20 +758,22 @@ __global__ void __launch_bounds__(256) k_naive(NaiveArgs a) {
     }
 }
 
-template <int FMT, bool U64, bool SMEM, bool LEVELS, int EPI>
+template <int FMT, bool U64, bool SMEM, bool LEVELS, int EPI, int D>
 void *alias_kernel_ptr() {
-    return reinterpret_cast<void *>(&k_alias<FMT, U64, SMEM, LEVELS, EPI>);
+    // per-level tables take one draw per group: the draw count never applies
+    return reinterpret_cast<void *>(&k_alias<FMT, U64, SMEM, LEVELS, EPI, LEVELS ? 0 : D>);
 }
 
 using KernelFn = void *(*)();
-#define RMAT_K2(F, U, S, L) \
-    {alias_kernel_ptr<F, U, S, L, 0>, alias_kernel_ptr<F, U, S, L, 1>, alias_kernel_ptr<F, U, S, L, 2>, \
-     alias_kernel_ptr<F, U, S, L, 3>}
-#define RMAT_K4(F, U, S) {RMAT_K2(F, U, S, false), RMAT_K2(F, U, S, true)}
-#define RMAT_K8(F, U) {RMAT_K4(F, U, false), RMAT_K4(F, U, true)}
-// [format][u64][shared table][per-level][epilogue: undirected | relabel << 1]
-KernelFn alias_kernel_table[2][2][2][2][4] = {{RMAT_K8(0, false), RMAT_K8(0, true)},
-                                              {RMAT_K8(1, false), RMAT_K8(1, true)}};
+#define RMAT_K2(D, F, U, S, L) \
+    {alias_kernel_ptr<F, U, S, L, 0, D>, alias_kernel_ptr<F, U, S, L, 1, D>, alias_kernel_ptr<F, U, S, L, 2, D>, \
+     alias_kernel_ptr<F, U, S, L, 3, D>}
+#define RMAT_K4(D, F, U, S) {RMAT_K2(D, F, U, S, false), RMAT_K2(D, F, U, S, true)}
+#define RMAT_K8(D, F, U) {RMAT_K4(D, F, U, false), RMAT_K4(D, F, U, true)}
+#define RMAT_K16(D) {{RMAT_K8(D, 0, false), RMAT_K8(D, 0, true)}, {RMAT_K8(D, 1, false), RMAT_K8(D, 1, true)}}
+// [phase-1 draws known to be 4][format][u64][shared table][per-level][epilogue: undirected | relabel << 1]
+KernelFn alias_kernel_table[2][2][2][2][2][4] = {RMAT_K16(0), RMAT_K16(4)};
+#undef RMAT_K16
 #undef RMAT_K8
 #undef RMAT_K4
 #undef RMAT_K2
@@ -901,6 +907,13 @@ rmat_status launch_kron(const rmat_table *t, const uint32_t *dblob, const AliasP
     return RMAT_OK;
 }
 
+// Draws of phase 1 (one Philox block): as many as k levels can need, at most
+// four -- ceil(k / shortest path with non-zero weight).
+int phase1_draws(const rmat_table *t) {
+    const int min_len = std::max(1, t->groups[0].min_len);
+    return std::max(1, std::min(4, (t->k + min_len - 1) / min_len));
+}
+
 rmat_status plan_alias_launch(const rmat_table *t, const rmat_launch_config_t &want, AliasPlan &plan) {
     DeviceProps props;
     if (rmat_status st = device_props(props)) return st;
@@ -941,7 +954,8 @@ rmat_status plan_alias_launch(const rmat_table *t, const rmat_launch_config_t &w
     plan.threads = threads;
     plan.tile = tile;
     plan.smem_bytes = need(smem_table, threads, tile);
-    plan.kernel = alias_kernel_table[plan.fmt][u64][smem_table][levels]
+    const int d4 = phase1_draws(t) == 4 ? 1 : 0;
+    plan.kernel = alias_kernel_table[d4][plan.fmt][u64][smem_table][levels]
                                     [((t->flags & RMAT_UNDIRECTED) ? kEpiUndir : 0) | (t->scramble ? kEpiScr : 0)]();
     cudaError_t e = set_smem_attr(plan.kernel, plan.smem_bytes);
     if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
@@ -958,12 +972,10 @@ rmat_status plan_alias_launch(const rmat_table *t, const rmat_launch_config_t &w
 Job make_job(const rmat_table *t, const uint32_t *dblob, bool smem, uint64_t seed, uint64_t e0, uint64_t count,
              void *out) {
     Job J{};
-    const PathTable &g0 = t->groups[0];
     J.blob = dblob;
     J.blob_bytes = uint32_t(t->image.size() * 4);
     J.k = t->k;
-    const int need_draws = (t->k + std::max(1, g0.min_len) - 1) / std::max(1, g0.min_len);
-    J.draws1 = std::max(1, std::min(4, need_draws));
+    J.draws1 = phase1_draws(t);
     J.ngroups = int(t->groups.size());
     J.levels = t->per_level ? 1u : 0u;
     J.flags = t->flags;

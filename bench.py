@@ -85,7 +85,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-sample-edges", type=int, default=1 << 27)
+    ap.add_argument("--no-mix", action="store_true", help="c2: leave out the batched and served measurements")
+    ap.add_argument("--cpu-sample-edges", type=int, default=1 << 30)
     ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5", "part", "kron", "tablebuild", "fig1"],
                     default="c2",
                     help="c2 (default): the contract line; c1/c3/c4/c5: the other configurations, one JSON line each")
@@ -320,6 +321,11 @@ def run_ours(args):
                "path": "rmat_build_table + rmat_table_upload + rmat_generate_host into pinned host memory"}
         del host
 
+    # the metric's second half: batched and served generation on this GPU
+    batched = served = None
+    if world == 1 and not args.no_mix:
+        batched = measure_batched()
+        served = measure_served()
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -347,6 +353,8 @@ def run_ours(args):
                                           "overhead_ns_per_edge": (scr_s - avg_launch_s) / m * 1e9,
                                           "note": "same launch with rmat_table_set_scramble on"}},
         "e2e": e2e,
+        "batched": batched,
+        "served": served,
         "gpu_launches": args.steps,
         "clocks": {"sm_mhz": cs["sm_mhz"], "sm_max_mhz": cs["sm_max_mhz"], "reasons": cs["reasons"]},
     }
@@ -429,6 +437,84 @@ def run_c3(args):
                       "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                                    "peak_source": src},
                       "clocks": clocks.summary()}), flush=True)
+
+
+def measure_batched(n_graphs: int = 512):
+    """The first n_graphs graphs of the 4096-graph batched workload in one
+    persistent launch (captured in a CUDA graph, replayed) against a
+    CUDA-graph-captured loop of one rmat_generate per graph and the same loop
+    launched eagerly, every graph's bytes compared between the two."""
+    import torch
+    import paper_1905_03525_gb300 as rm
+    from paper_1905_03525_gb300 import autotune
+    from paper_1905_03525_gb300.workloads import batched_graphs
+    graphs = batched_graphs(4096)[:n_graphs]
+    tables, choices = autotune.plan_batch(graphs)
+    offs, off = [], 0
+    for g in graphs:
+        offs.append(off)
+        off += (g["m"] + 63) // 64 * 64
+    arenas = [torch.empty((off, 2), dtype=torch.int32, device="cuda") for _ in range(2)]
+    outs = [[a[o:o + g["m"]] for o, g in zip(offs, graphs)] for a in arenas]
+    s = torch.cuda.Stream()
+    b = rm.rmat_batch_create()
+    for g, t, o in zip(graphs, tables, outs[0]):
+        rm.rmat_batch_add(b, t, g["seed"], 0, g["m"], o)
+    rm.rmat_batch_prepare(b)
+
+    def loop():
+        for g, t, o in zip(graphs, tables, outs[1]):
+            rm.rmat_generate(t, g["seed"], 0, g["m"], o, s)
+
+    gb, gl = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gb, stream=s):
+        rm.rmat_batch_launch(b, s)
+    loop()  # plans and uploads every table before capture
+    with torch.cuda.graph(gl, stream=s):
+        loop()
+    with torch.cuda.stream(s):
+        gb.replay()
+        gl.replay()
+        t_batch = _events_time(gb.replay, s, 3)
+        t_graph = _events_time(gl.replay, s, 3)
+    t_eager = _events_time(loop, s, 2)
+    same = bool(torch.equal(arenas[0], arenas[1]))
+    rm.rmat_check_device_errors()
+    edges = sum(g["m"] for g in graphs)
+    b.free()
+    del gb, gl, arenas, outs
+    torch.cuda.empty_cache()
+    return {"graphs": n_graphs, "edges": edges,
+            "workload": f"graphs 0..{n_graphs - 1} of the batched workload: k~U{{10..24}}, m=round(2^U(12,26)), "
+                        "(a,b,c,d)~Dirichlet(57,19,19,5), seed=4096+i, u32; tables as the autotuner picks them",
+            "batched_edges_per_s": edges / t_batch, "per_graph_cuda_graph_edges_per_s": edges / t_graph,
+            "per_graph_eager_edges_per_s": edges / t_eager, "speedup_vs_graphed_loop": t_graph / t_batch,
+            "speedup_vs_eager": t_eager / t_batch, "bytes_identical": same,
+            "timing": "one captured persistent launch vs one captured per-graph loop, 3 replays each, CUDA events",
+            "table_choice_per_k": {str(k): v for k, v in sorted(choices.items())}}
+
+
+def measure_served(n_requests: int = 64, rate: float = 2000.0):
+    """A short served trace: n_requests Poisson arrivals at `rate` per second
+    through the continuous-batching server, against the same trace with one
+    request on the GPU at a time."""
+    from paper_1905_03525_gb300 import serve
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    budget = min(160 * 10 ** 9, int(free * 0.8))
+    trace = serve.served_trace(n_requests, rate=rate)
+    res = {}
+    for name, active in (("continuous_batching", 64), ("one_request_at_a_time", 1)):
+        with serve.Server(budget, chunk_edges=1 << 28, step_edges=1 << 31, max_active=active) as srv:
+            srv.wait(srv.submit(*G500, 16, 1 << 20, 1))  # warm-up request
+            res[name] = serve.summarise(serve.run_trace(srv, trace))
+    return {"requests": n_requests, "rate_per_s": rate, "hbm_budget_bytes": budget,
+            "workload": "Poisson arrivals, k~U{12..30}, ef in {4,8,16,32}, m=ef*2^k, "
+                        "(a,b,c,d)~Dirichlet(57,19,19,5), 2^28-edge chunks",
+            **res, "speedup_vs_one_at_a_time": res["continuous_batching"]["edges_per_s"] /
+            res["one_request_at_a_time"]["edges_per_s"],
+            "p50_vs_one_at_a_time": res["one_request_at_a_time"]["p50_latency_s"] /
+            res["continuous_batching"]["p50_latency_s"]}
 
 
 def run_c4(args):

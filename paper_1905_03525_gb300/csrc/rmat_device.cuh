@@ -145,6 +145,7 @@ struct Group {
     uint32_t sA, sBs, sBa;            // shared byte addresses (SMEM)
     const uint32_t *gA, *gBs, *gBa;   // global addresses (!SMEM)
     uint32_t shb;                     // 32 - b: column j = u >> (32 - b)
+    uint32_t one;                     // 1, known only at run time (see Acc32::append)
 };
 
 // Blob header word `w` (group descriptors), from shared or global memory.
@@ -168,6 +169,7 @@ __device__ __forceinline__ Group<SMEM> group(uint32_t sbase, const uint32_t *gbl
     G.gBs = gblob + bsoff;
     G.gBa = gblob + baoff;
     G.shb = 32u - bits;
+    G.one = 1u;
     return G;
 }
 
@@ -183,10 +185,14 @@ struct Acc32 {
         col = c;
         filled = L;
     }
-    // Any number of levels may be appended: shifts of 32 or more give 0.
-    __device__ __forceinline__ void append(uint32_t r, uint32_t c, uint32_t L) {
-        row |= shr_clamp(r, filled);
-        col |= shr_clamp(c, filled);
+    // Any number of levels may be appended: shifts of 32 or more give 0.  The
+    // path's bits land below the `filled` levels already present, so OR-ing
+    // them in is an add; written as a multiply-add by a run-time 1 it issues
+    // on the FMA pipe, leaving the ALU pipe (shifts, compares, selects of the
+    // draw) less loaded -- the ALU pipe is the one that bounds the kernel.
+    __device__ __forceinline__ void append(uint32_t r, uint32_t c, uint32_t L, uint32_t one) {
+        row = shr_clamp(r, filled) * one + row;
+        col = shr_clamp(c, filled) * one + col;
         filled += L;
     }
     __device__ __forceinline__ uint64_t out_row(int k) const { return row >> (32 - k); }
@@ -203,7 +209,7 @@ struct Acc64 {
         filled = L;
     }
     // Only called while filled < k <= 64.
-    __device__ __forceinline__ void append(uint32_t r, uint32_t c, uint32_t L) {
+    __device__ __forceinline__ void append(uint32_t r, uint32_t c, uint32_t L, uint32_t /*one*/) {
         row |= (uint64_t(r) << 32) >> filled;
         col |= (uint64_t(c) << 32) >> filled;
         filled += L;
@@ -252,7 +258,7 @@ __device__ __forceinline__ void draw(const Group<SMEM> &G, uint32_t u, Acc &acc)
         }
     }
     if constexpr (FIRST) acc.set(r, c, L);
-    else acc.append(r, c, L);
+    else acc.append(r, c, L, G.one);
 }
 
 // The same draw from a table of fixed-length paths (every entry has exactly

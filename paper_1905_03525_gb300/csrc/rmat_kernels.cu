@@ -74,6 +74,7 @@ __device__ __forceinline__ dev::Group<SMEM> group0(const Job &J, uint32_t sblob)
     G.gBs = J.blob + J.bs0;
     G.gBa = J.blob + J.ba0;
     G.shb = 32u - J.bits0;
+    G.one = J.one;
     return G;
 }
 
@@ -203,18 +204,21 @@ __device__ __forceinline__ uint32_t phase1(const Job &J, const K &ks, const Scra
     auto step = [&](Acc &acc, uint32_t u) {
         if (!U64 || acc.filled < uk) dev::draw<FMT, SMEM>(G0, u, acc);
     };
+    using Word = typename AccT<U64>::word;
+    constexpr uint32_t W = U64 ? 64u : 32u;
+    const uint32_t sh = W - uk;
     auto settle = [&](const Acc &acc, uint32_t it) {
         const uint32_t idx = it * 32 + lane;
         if (!FULL && idx >= n) return;
         const bool done = acc.filled >= uk;
-        uint64_t r = done ? acc.out_row(J.k) : uint64_t(acc.row);
-        uint64_t c = done ? acc.out_col(J.k) : uint64_t(acc.col);
+        Word r = done ? Word(acc.row >> sh) : acc.row;
+        Word c = done ? Word(acc.col >> sh) : acc.col;
         if (relabel<EPI>(J) && done) {
             r = scramble_id<U64>(acc.row, J, S);
             c = scramble_id<U64>(acc.col, J, S);
         }
         if ((EPI & kEpiUndir) && done && r > c) {
-            const uint64_t t = r;
+            const Word t = r;
             r = c;
             c = t;
         }
@@ -235,7 +239,6 @@ __device__ __forceinline__ uint32_t phase1(const Job &J, const K &ks, const Scra
         for (int q = 0; q < E; ++q) w[q] = edge_block(ks, 0u, ebase + (it + q) * 32 + lane);
         if constexpr (PRE) {
             // batched jobs may start below the top level (a partition tile)
-            using Word = typename AccT<U64>::word;
 #pragma unroll
             for (int q = 0; q < E; ++q) {
                 a[q].row = Word(J.pre_row);
@@ -260,8 +263,8 @@ __device__ __forceinline__ uint32_t phase1(const Job &J, const K &ks, const Scra
             for (int q = 0; q < E; ++q) step(a[q], w[q].w);
         }
 #pragma unroll
-        for (int q = 0; q < E; ++q)
-            if (q == 0 || it + q < iters) settle(a[q], it + q);  // a tile may end inside the group
+        for (int q = 0; q < E; ++q)  // a tile of FULL edges holds whole groups; others may end inside one
+            if (FULL || q == 0 || it + q < iters) settle(a[q], it + q);
     }
     return pm;
 }
@@ -271,8 +274,9 @@ __device__ __forceinline__ uint32_t phase1(const Job &J, const K &ks, const Scra
 // them from the blob header at every draw.
 // ks: where the Philox round keys come from (see edge_block).  PRE: edges
 // start with the job's prefix levels (batched jobs).  D: phase 1's draw count
-// when known at compile time (4), else 0.
-template <int FMT, bool U64, bool SMEM, bool LEVELS, int EPI, bool PRE, int D, class K>
+// when known at compile time (4), else 0.  FULL: the tile is known to hold
+// W.tile edges (otherwise chosen at run time from n).
+template <int FMT, bool U64, bool SMEM, bool LEVELS, int EPI, bool PRE, int D, bool FULL, class K>
 __device__ __forceinline__ void gen_tile(const Job &J, const K &ks, const Scramble &S, uint32_t sblob,
                                          const uint32_t *gblob, const dev::Group<SMEM> &G0, uint64_t first,
                                          uint32_t n, WarpState &W, uint32_t sgroups = 0) {
@@ -346,7 +350,8 @@ __device__ __forceinline__ void gen_tile(const Job &J, const K &ks, const Scramb
             }
         }
     } else {
-        const uint32_t pm = n == uint32_t(W.tile)
+        // whole groups of E edges per lane (E <= 4): phase 1 without edge guards
+        const uint32_t pm = (FULL || (n == uint32_t(W.tile) && n % 128u == 0))
                                 ? phase1<FMT, U64, SMEM, EPI, true, PRE, D>(J, ks, S, G0, ebase, n, stage, p_fill, lane)
                                 : phase1<FMT, U64, SMEM, EPI, false, PRE, D>(J, ks, S, G0, ebase, n, stage, p_fill, lane);
         // Phase 2: queue the unfinished edges of the whole tile (warp prefix
@@ -487,14 +492,23 @@ __global__ void __launch_bounds__(1024, 1) k_alias(const __grid_constant__ Job J
     W.tile = tile;
     W.issued = false;
     W.lane = lane;
-    const uint64_t ntiles = (J.count + tile - 1) / tile;
+    // full tiles round-robin over the warps, then the ragged last tile (if
+    // any) on the warp whose turn it is
+    const uint64_t nfull = J.count / uint64_t(tile);
     const uint64_t stride = uint64_t(gridDim.x) * nwarps;
-    for (uint64_t t = uint64_t(blockIdx.x) * nwarps + warp; t < ntiles; t += stride) {
-        const uint64_t first = t * tile;
-        const uint64_t left = J.count - first;
-        const uint32_t n = left < uint64_t(tile) ? uint32_t(left) : uint32_t(tile);
-        gen_tile<FMT, U64, SMEM, LEVELS, EPI, false, D>(J, J.ks, S, sblob, J.blob, G0, first, n, W, sgroups);
+    uint64_t t = uint64_t(blockIdx.x) * nwarps + warp;
+    if (tile % 128 == 0) {
+        for (; t < nfull; t += stride)
+            gen_tile<FMT, U64, SMEM, LEVELS, EPI, false, D, true>(J, J.ks, S, sblob, J.blob, G0, t * tile,
+                                                                   uint32_t(tile), W, sgroups);
+    } else {
+        for (; t < nfull; t += stride)
+            gen_tile<FMT, U64, SMEM, LEVELS, EPI, false, D, false>(J, J.ks, S, sblob, J.blob, G0, t * tile,
+                                                                    uint32_t(tile), W, sgroups);
     }
+    if (t == nfull && J.count % uint64_t(tile))
+        gen_tile<FMT, U64, SMEM, LEVELS, EPI, false, D, false>(J, J.ks, S, sblob, J.blob, G0, t * tile,
+                                                                uint32_t(J.count % uint64_t(tile)), W, sgroups);
     if (lane == 0 && W.issued) dev::bulk_wait_all();
 }
 
@@ -509,7 +523,7 @@ __device__ __forceinline__ void batch_unit(const Job &J, const Scramble &S, Shar
     for (uint64_t first = f0 + uint64_t(warp) * W.tile; first < end; first += uint64_t(nwarps) * W.tile) {
         const uint64_t left = end - first;
         const uint32_t n = left < uint64_t(W.tile) ? uint32_t(left) : uint32_t(W.tile);
-        gen_tile<FMT, U64, SMEM, LEVELS, EPI, PRE, 0>(J, ks, S, sblob, J.blob, G0, first, n, W);
+        gen_tile<FMT, U64, SMEM, LEVELS, EPI, PRE, 0, false>(J, ks, S, sblob, J.blob, G0, first, n, W);
     }
 }
 
@@ -975,6 +989,7 @@ Job make_job(const rmat_table *t, const uint32_t *dblob, bool smem, uint64_t see
     J.blob = dblob;
     J.blob_bytes = uint32_t(t->image.size() * 4);
     J.k = t->k;
+    J.one = 1u;
     J.draws1 = phase1_draws(t);
     J.ngroups = int(t->groups.size());
     J.levels = t->per_level ? 1u : 0u;

@@ -33,6 +33,7 @@ struct Job {
     uint32_t levels;       // draw g uses group g
     uint32_t a0, bs0, ba0; // group 0: word offsets of A, Bs, Ba in the blob
     uint32_t bits0;        // group 0: b
+    uint32_t one;          // 1 (a multiplier the compiler cannot fold: see dev::Acc32::append)
     uint64_t unit_begin;   // first work unit of this job (batches)
     // Batched jobs only: levels fixed before the first draw (the tile of a
     // partitioned graph), left-aligned in the accumulator word.

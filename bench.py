@@ -742,9 +742,29 @@ def run_tablebuild(args):
             oracle.Table.variable(*G500, K, bound)
             row["oracle_ms"] = (time.perf_counter() - t0) * 1e3
         rows.append(row)
+    # serving: a request with a large explicit bound, from the client's submit
+    # call to its admission, with the table built on the submitting thread
+    # (host) or by the server's builder thread (GPU), and the submit call itself
+    from paper_1905_03525_gb300 import serve
+    served = []
+    for bound in (1 << 16, 1 << 18, 1 << 20):
+        row = {"bound": bound}
+        for mode, min_bound in (("host_build", 0), ("gpu_build", 1 << 14)):
+            with serve.Server(1 << 30, chunk_edges=1 << 20, step_edges=1 << 22, max_active=4,
+                              gpu_build_min_bound=min_bound) as srv:
+                srv.wait(srv.wait(srv.submit(*G500, K, 1 << 16, 1, bound))["id"])  # warm: caches, kernels
+                clock0 = srv.stats()["clock_s"]
+                t0 = time.perf_counter()
+                rid = srv.submit(*G500, K, 1 << 20, 2, bound)
+                call_ms = (time.perf_counter() - t0) * 1e3
+                st = srv.wait(rid)
+            row[mode] = {"submit_call_ms": call_ms, "admission_ms": (st["admit_s"] - clock0) * 1e3,
+                         "latency_ms": (st["done_s"] - clock0) * 1e3}
+        served.append(row)
     print(json.dumps({"workload": "tablebuild", "config": {"workload": "variable-length table, G500 parameters, "
-                      "k=26; wall time of one build call including copies back to the host"},
-                      "metric": "ms per table", "rows": rows}), flush=True)
+                      "k=26; wall time of one build call including copies back to the host; served: one request of "
+                      "2^20 edges with that bound, from the client's submit call"},
+                      "metric": "ms per table", "rows": rows, "served": served}), flush=True)
 
 
 def main():

@@ -381,6 +381,9 @@ typedef struct {
     uint64_t step_edges;       /* edges per step over all requests (>= chunk_edges) */
     int max_active;            /* requests generated concurrently, 1..4096 */
     double wait_timeout_s;     /* host-side bound on one step; beyond it the step's requests fail */
+    uint64_t gpu_build_min_bound; /* requests with an explicit table_bound >= this have their table built on
+                                     the GPU (rmat_build_table_gpu) by the server's builder thread, off the
+                                     submitting thread; 0 = every table on the submitting thread */
 } rmat_server_config_t;
 
 typedef struct {
@@ -425,7 +428,10 @@ typedef void (*rmat_chunk_fn)(void *user, uint64_t request_id, uint64_t edge_off
  * worker. */
 rmat_status rmat_server_create(const rmat_server_config_t *cfg, rmat_server **out);
 rmat_status rmat_server_set_chunk_callback(rmat_server *s, rmat_chunk_fn fn, void *user);
-/* Build the request's table on the calling thread and queue it.  Thread-safe.
+/* Build the request's table on the calling thread (or, for an explicit
+ * table_bound >= gpu_build_min_bound, hand it to the server's builder thread,
+ * which builds it on the GPU; the request is admitted once it is ready) and
+ * queue the request.  Thread-safe.
  * RMAT_ERR_OUT_OF_MEMORY if the request could never fit the budget. */
 rmat_status rmat_server_submit(rmat_server *s, const rmat_request_t *req, uint64_t *id);
 rmat_status rmat_server_status(rmat_server *s, uint64_t id, rmat_request_status_t *st);

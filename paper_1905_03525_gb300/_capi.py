@@ -38,7 +38,8 @@ class TableInfo(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("chunk_edges", ctypes.c_uint64),
-                ("step_edges", ctypes.c_uint64), ("max_active", ctypes.c_int), ("wait_timeout_s", ctypes.c_double)]
+                ("step_edges", ctypes.c_uint64), ("max_active", ctypes.c_int), ("wait_timeout_s", ctypes.c_double),
+                ("gpu_build_min_bound", ctypes.c_uint64)]
 
 
 class Request(ctypes.Structure):

@@ -15,6 +15,11 @@
 //              its slot at once, and queued requests are admitted before the
 //              next step, so new work joins the GPU while other requests are
 //              still being generated.
+// Tables of requests with a large explicit bound (>= gpu_build_min_bound) are
+// built on the GPU (Sec. 3 parallel construction, rmat_build_table_gpu) by a
+// builder thread on its own stream: submit returns at once, and admission
+// takes such a request once its table is ready (requests behind it in the
+// queue are not held up).  Smaller tables are built on the submitting thread.
 // Every edge's bytes depend only on (table, seed, edge index), so a request's
 // output and checksum are the same alone and in any mix.
 #include <cuda_runtime.h>
@@ -90,6 +95,7 @@ struct Request {
     uint64_t buf_edges = 0;
     double t_submit = 0, t_admit = 0, t_done = 0;
     rmat_status err = RMAT_OK;
+    bool ready = true;         // table built (false while the builder thread works on it)
 };
 
 }  // namespace
@@ -104,6 +110,10 @@ struct rmat_server {
     bool stop = false;
     std::thread worker;
     std::deque<rmat::Request *> queue;
+    std::deque<rmat::Request *> to_build;  // requests whose table the builder thread makes
+    std::condition_variable cv_build;
+    std::thread builder;
+    cudaStream_t build_stream = nullptr;
     std::vector<rmat::Request *> active;
     std::map<uint64_t, rmat::Request *> all;
     uint64_t next_id = 1;
@@ -157,10 +167,15 @@ void finish(rmat_server *s, Request *r, int state, rmat_status err) {
     }
 }
 
-// Admit queued requests (FIFO) while a slot is free and memory fits.
+// Admit queued requests in FIFO order while a slot is free and memory fits;
+// requests whose table is still being built are passed over.
 void admit(rmat_server *s) {
-    while (!s->queue.empty() && int(s->active.size()) < s->cfg.max_active) {
-        Request *r = s->queue.front();
+    for (auto it = s->queue.begin(); it != s->queue.end() && int(s->active.size()) < s->cfg.max_active;) {
+        Request *r = *it;
+        if (!r->ready) {
+            ++it;
+            continue;
+        }
         const uint64_t eb = r->table->k > 32 ? 16 : 8;
         const size_t blob = r->table->image.size() * 4;
         const uint64_t edges = std::min<uint64_t>(r->desc.m, s->cfg.chunk_edges);
@@ -170,7 +185,7 @@ void admit(rmat_server *s) {
             s->arena->release(boff, blob);
             break;
         }
-        s->queue.pop_front();
+        it = s->queue.erase(it);
         r->blob_off = boff;
         r->blob_bytes = blob;
         r->buf_off = coff;
@@ -277,7 +292,7 @@ void worker_main(rmat_server *s) {
     for (;;) {
         admit(s);
         if (s->active.empty()) {
-            if (s->stop && s->queue.empty()) break;
+            if (s->stop && s->queue.empty() && s->to_build.empty()) break;
             s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
             continue;
         }
@@ -331,6 +346,50 @@ void worker_main(rmat_server *s) {
     }
 }
 
+// Build the request's table (GPU construction, host construction when the
+// parameters are outside the GPU build's range) with its flags and
+// relabelling.
+rmat_status build_request_table(rmat_server *s, const rmat_request_t &q, uint64_t bound, bool on_gpu,
+                                rmat_table **out) {
+    rmat_table *t = nullptr;
+    rmat_status st = RMAT_ERR_UNSUPPORTED;
+    if (on_gpu) st = rmat_build_table_gpu(q.a, q.b, q.c, q.d, q.k, bound, reinterpret_cast<rmat_stream_t>(s->build_stream), &t);
+    if (st == RMAT_ERR_UNSUPPORTED) st = rmat_build_table(q.a, q.b, q.c, q.d, q.k, bound, &t);
+    if (st == RMAT_OK) st = rmat_table_set_flags(t, q.flags);
+    if (st == RMAT_OK) st = rmat_table_set_scramble(t, q.scramble, q.scramble_seed);
+    if (st != RMAT_OK) {
+        if (t) rmat_free_table(t);
+        return st;
+    }
+    *out = t;
+    return RMAT_OK;
+}
+
+void builder_main(rmat_server *s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        while (s->to_build.empty() && !s->stop) s->cv_build.wait(lk);
+        if (s->to_build.empty()) break;
+        Request *r = s->to_build.front();
+        s->to_build.pop_front();
+        const rmat_request_t q = r->desc;
+        lk.unlock();
+        rmat_table *t = nullptr;
+        const rmat_status st = build_request_table(s, q, q.table_bound, true, &t);
+        lk.lock();
+        if (st != RMAT_OK) {
+            s->queue.erase(std::find(s->queue.begin(), s->queue.end(), r));
+            finish(s, r, RMAT_REQ_FAILED, st);
+            s->cv_done.notify_all();
+            continue;
+        }
+        r->table = t;
+        r->ready = true;
+        s->cv_work.notify_one();
+    }
+}
+
 template <class T>
 rmat_status dev_alloc(T **p, size_t bytes) {
     if (cudaMalloc(reinterpret_cast<void **>(p), std::max<size_t>(bytes, 256)) != cudaSuccess) {
@@ -362,6 +421,7 @@ void free_server(rmat_server *s) {
     if (s->h_units) cudaFreeHost(s->h_units);
     if (s->h_sums) cudaFreeHost(s->h_sums);
     if (s->stream) cudaStreamDestroy(s->stream);
+    if (s->build_stream) cudaStreamDestroy(s->build_stream);
     for (auto &kv : s->all) {
         if (kv.second->table) rmat_free_table(kv.second->table);
         delete kv.second;
@@ -403,7 +463,8 @@ rmat_status rmat_server_create(const rmat_server_config_t *cfg, rmat_server **ou
     s->t0 = Clock::now();
     cudaGetDevice(&s->device);
     rmat_status st = device_props(s->props);
-    if (st == RMAT_OK && cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess)
+    if (st == RMAT_OK && (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+                          cudaStreamCreateWithFlags(&s->build_stream, cudaStreamNonBlocking) != cudaSuccess))
         st = fail(RMAT_ERR_CUDA, "stream creation failed");
     if (st == RMAT_OK) st = dev_alloc(&s->arena_dev, cfg->hbm_budget_bytes);
     // Work list of one step: at most max_active jobs and
@@ -425,6 +486,7 @@ rmat_status rmat_server_create(const rmat_server_config_t *cfg, rmat_server **ou
     }
     s->arena = new Arena(cfg->hbm_budget_bytes);
     s->worker = std::thread(worker_main, s);
+    s->builder = std::thread(builder_main, s);
     *out = s;
     return RMAT_OK;
 }
@@ -450,28 +512,36 @@ rmat_status rmat_server_submit(rmat_server *s, const rmat_request_t *req, uint64
     const size_t smem_budget = size_t(s->props.max_smem) - kBatchHeaderBytes -
                                size_t(kThreads / 32) * warp_bytes(u64, false, tile_for(u64));
     uint64_t bound = req->table_bound ? req->table_bound : 8192;
-    rmat_table *t = nullptr;
-    for (;;) {
-        if (rmat_status st = rmat_build_table(req->a, req->b, req->c, req->d, req->k, bound, &t)) return st;
-        if (req->table_bound || t->image.size() * 4 <= smem_budget || bound <= 64) break;
-        rmat_free_table(t);
-        t = nullptr;
-        bound /= 2;
-    }
-    if (rmat_status st = rmat_table_set_flags(t, req->flags)) {
-        rmat_free_table(t);
-        return st;
-    }
-    if (rmat_status st = rmat_table_set_scramble(t, req->scramble, req->scramble_seed)) {
-        rmat_free_table(t);
-        return st;
-    }
     const uint64_t eb = req->k > 32 ? 16 : 8;
-    const uint64_t need = ((t->image.size() * 4 + 255) & ~uint64_t(255)) +
-                          ((std::min<uint64_t>(req->m, s->cfg.chunk_edges) * eb + 255) & ~uint64_t(255));
-    if (need > s->cfg.hbm_budget_bytes) {
-        rmat_free_table(t);
-        return fail(RMAT_ERR_OUT_OF_MEMORY, "request needs more device memory than the server's whole budget");
+    const uint64_t chunk_bytes = (std::min<uint64_t>(req->m, s->cfg.chunk_edges) * eb + 255) & ~uint64_t(255);
+    const bool on_gpu = req->table_bound && s->cfg.gpu_build_min_bound && req->table_bound >= s->cfg.gpu_build_min_bound;
+    rmat_table *t = nullptr;
+    if (on_gpu) {
+        // checked now with the largest image a table of this bound can have
+        // (wide entries: 36 bytes per column of the padded size)
+        if (req->table_bound < 5 || req->table_bound > (uint64_t(1) << 24) || req->k < 1 || req->k > 64)
+            return fail(RMAT_ERR_INVALID_ARGUMENT, "table_bound must be in [5, 2^24] and k in [1, 64]");
+        const double in[4] = {req->a, req->b, req->c, req->d};
+        double P[4];
+        if (rmat_status st = normalise_params(in, P)) return st;
+        uint64_t N = 1;
+        while (N < req->table_bound) N <<= 1;
+        const uint64_t image_max = ((4 * kHeaderWords + 36 * N + 64) + 255) & ~uint64_t(255);
+        if (image_max + chunk_bytes > s->cfg.hbm_budget_bytes)
+            return fail(RMAT_ERR_OUT_OF_MEMORY, "request needs more device memory than the server's whole budget");
+    } else {
+        for (;;) {
+            if (rmat_status st = build_request_table(s, *req, bound, false, &t)) return st;
+            if (req->table_bound || t->image.size() * 4 <= smem_budget || bound <= 64) break;
+            rmat_free_table(t);
+            t = nullptr;
+            bound /= 2;
+        }
+        const uint64_t need = ((t->image.size() * 4 + 255) & ~uint64_t(255)) + chunk_bytes;
+        if (need > s->cfg.hbm_budget_bytes) {
+            rmat_free_table(t);
+            return fail(RMAT_ERR_OUT_OF_MEMORY, "request needs more device memory than the server's whole budget");
+        }
     }
     Request *r = new (std::nothrow) Request;
     if (!r) {
@@ -481,14 +551,17 @@ rmat_status rmat_server_submit(rmat_server *s, const rmat_request_t *req, uint64
     r->desc = *req;
     r->desc.table_bound = bound;
     r->table = t;
+    r->ready = !on_gpu;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         r->id = s->next_id++;
         r->t_submit = now_s(s);
         s->all[r->id] = r;
         s->queue.push_back(r);
+        if (on_gpu) s->to_build.push_back(r);
     }
-    s->cv_work.notify_one();
+    if (on_gpu) s->cv_build.notify_one();
+    else s->cv_work.notify_one();
     if (id) *id = r->id;
     return RMAT_OK;
 }
@@ -554,6 +627,13 @@ void rmat_server_destroy(rmat_server *s) {
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;
+        s->to_build.clear();
+    }
+    // the builder finishes the table it is making, then stops
+    s->cv_build.notify_all();
+    if (s->builder.joinable()) s->builder.join();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
         // requests still queued are failed without running
         while (!s->queue.empty()) {
             finish(s, s->queue.front(), RMAT_REQ_FAILED, RMAT_ERR_INVALID_ARGUMENT);

@@ -22,8 +22,12 @@ class Server:
     """A librmat generation server on the current CUDA device."""
 
     def __init__(self, hbm_budget_bytes: int, chunk_edges: int = 1 << 28, step_edges: int = 1 << 31,
-                 max_active: int = 64, wait_timeout_s: float = 120.0):
-        cfg = ServerConfig(hbm_budget_bytes, chunk_edges, max(step_edges, chunk_edges), max_active, wait_timeout_s)
+                 max_active: int = 64, wait_timeout_s: float = 120.0, gpu_build_min_bound: int = 1 << 14):
+        """gpu_build_min_bound: requests with an explicit table bound at least
+        this large get their table built on the GPU by the server's builder
+        thread (0: every table is built on the host when submitted)."""
+        cfg = ServerConfig(hbm_budget_bytes, chunk_edges, max(step_edges, chunk_edges), max_active, wait_timeout_s,
+                           gpu_build_min_bound)
         h = ctypes.c_void_p()
         check(lib().rmat_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h

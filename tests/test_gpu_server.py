@@ -169,6 +169,27 @@ def test_served_bytes_match_oracle():
         assert st["checksum"] == host_checksum(r, c, 0), (k, fl, scr)
 
 
+def test_large_bound_tables_built_on_the_gpu():
+    """Requests with a large explicit bound get their table from the GPU
+    build on the server's builder thread (parameters outside its range fall
+    back to the host build); their bytes are the oracle's, and small requests
+    submitted behind them are not held up."""
+    reqs = [(G500, 26, 200_000, 31, 1 << 16), (SKEWED, 24, 100_003, 32, 1 << 15),
+            ((0.6, 0.2, 0.2, 0.0), 20, 50_000, 33, 1 << 14),   # d = 0: host build
+            (G500, 18, 30_000, 34, 0), ((0.45, 0.22, 0.22, 0.11), 22, 70_000, 35, 0)]
+    with Server(256 << 20, chunk_edges=1 << 16, step_edges=1 << 18, max_active=4,
+                gpu_build_min_bound=1 << 14) as srv:
+        ids = [srv.submit(*p, k, m, s, bound) for p, k, m, s, bound in reqs]
+        srv.drain(600)
+        sts = [srv.status(i) for i in ids]
+    for st, (p, k, m, s, bound) in zip(sts, reqs):
+        assert st["state"] == DONE and st["edges_done"] == m, st
+        if bound:
+            assert st["table_bound"] == bound
+        r, c = oracle_edges(p, k, m, s, st["table_bound"])
+        assert st["checksum"] == host_checksum(r, c, 0), (k, bound)
+
+
 def test_admission_backs_off_on_memory():
     # 1 MiB holds one request at a time (33 KiB table + 512 KiB chunk buffer)
     with Server(1 << 20, chunk_edges=1 << 16, step_edges=1 << 16, max_active=8) as srv:

@@ -64,6 +64,7 @@ struct AliasPlan {
     int sms = 0;
     size_t smem_bytes = 0;
     void *kernel = nullptr;
+    void *fast_kernel = nullptr;  // the contract-case kernel, when the table qualifies
     unsigned *err = nullptr;
 };
 

@@ -512,6 +512,117 @@ __global__ void __launch_bounds__(1024, 1) k_alias(const __grid_constant__ Job J
     if (lane == 0 && W.issued) dev::bulk_wait_all();
 }
 
+// The contract case of the single-graph kernel and nothing else: compact
+// entries, u32 IDs, the table in shared memory, one group, phase 1 known to
+// take four draws, the plain epilogue, whole tiles only (the tile a multiple of
+// 128 edges and the count a multiple of the tile) and a 16-byte-aligned
+// output.  The arithmetic is gen_tile's; it is a kernel of its own because the
+// compiler's split of the loop between the ALU and FMA pipes -- the two pipes
+// that bound this kernel -- shifts with any other code in the kernel (the
+// general kernel's ragged-tile and unaligned-store paths cost ~5 %).  The host
+// sends everything else, and the ragged tail of a launch, to k_alias.
+__global__ void __launch_bounds__(1024, 1) k_alias_fast(const __grid_constant__ Job J, int tile) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(J.blob);
+        uint4 *dst = reinterpret_cast<uint4 *>(smem);
+        for (uint32_t i = threadIdx.x; i < J.blob_bytes / 16; i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const uint32_t sblob = dev::smem_u32(smem);
+    const dev::Group<true> G = group0<true>(J, sblob);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t stage = sblob + J.blob_bytes + uint32_t(warp) * warp_region_bytes(false, false, tile);
+    const uint32_t p_fill = stage + 8u * uint32_t(tile), p_q = p_fill + uint32_t(tile);
+    const uint32_t uk = uint32_t(J.k), sh = 32u - uk;
+    const uint32_t iters = uint32_t(tile) / 32;
+    const uint64_t ntiles = J.count / uint64_t(tile);
+    bool issued = false;
+    for (uint64_t t = uint64_t(blockIdx.x) * nwarps + warp; t < ntiles; t += uint64_t(gridDim.x) * nwarps) {
+        const uint64_t first = t * uint64_t(tile);
+        const uint64_t ebase = J.e0 + first;
+        if (lane == 0 && issued) dev::bulk_wait_read_0();
+        __syncwarp();
+        // phase 1: one Philox block and four draws per edge, four edges per lane
+        uint32_t pm = 0;
+        for (uint32_t it = 0; it < iters; it += 4) {
+            uint4 w[4];
+            dev::Acc32 a[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint64_t e = ebase + (it + q) * 32 + lane;
+                w[q] = dev::philox_ks(0u, 0u, uint32_t(e), uint32_t(e >> 32), J.ks);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dev::draw<0, true, true>(G, w[q].x, a[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dev::draw<0, true>(G, w[q].y, a[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dev::draw<0, true>(G, w[q].z, a[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dev::draw<0, true>(G, w[q].w, a[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t idx = (it + q) * 32 + lane;
+                const bool done = a[q].filled >= uk;
+                dev::sts64(stage + 8u * idx, done ? a[q].row >> sh : a[q].row, done ? a[q].col >> sh : a[q].col);
+                dev::sts8(p_fill + idx, a[q].filled);
+                pm |= uint32_t(!done) << (it + q);
+            }
+        }
+        // phase 2: the unfinished edges of the tile, 32 at a time
+        const uint32_t cnt = __popc(pm);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total) {
+            uint32_t pos = incl - cnt;
+            for (uint32_t m = pm; m; m &= m - 1) dev::sts16(p_q + 2u * pos++, (__ffs(m) - 1) * 32 + lane);
+            __syncwarp();
+            for (uint32_t pb = 0; pb < total; pb += 32) {
+                const bool has = pb + lane < total;
+                dev::Acc32 acc;
+                acc.row = acc.col = 0;
+                acc.filled = uk;
+                uint32_t idx = 0;
+                if (has) {
+                    idx = dev::lds16(p_q + 2u * (pb + lane));
+                    const uint2 v = dev::lds64(stage + 8u * idx);
+                    acc.row = v.x;
+                    acc.col = v.y;
+                    acc.filled = dev::lds8(p_fill + idx);
+                }
+                const uint64_t e = ebase + idx;
+                for (uint32_t q = 1; q <= 17; ++q) {  // k <= 32 levels: at most 8 more blocks
+                    if (!__any_sync(0xffffffffu, acc.filled < uk)) break;
+                    const uint4 w = dev::philox_ks(q, 0u, uint32_t(e), uint32_t(e >> 32), J.ks);
+                    dev::draw<0, true>(G, w.x, acc);
+                    if (!__any_sync(0xffffffffu, acc.filled < uk)) break;
+                    dev::draw<0, true>(G, w.y, acc);
+                    if (!__any_sync(0xffffffffu, acc.filled < uk)) break;
+                    dev::draw<0, true>(G, w.z, acc);
+                    if (!__any_sync(0xffffffffu, acc.filled < uk)) break;
+                    dev::draw<0, true>(G, w.w, acc);
+                }
+                if (has) dev::sts64(stage + 8u * idx, acc.row >> sh, acc.col >> sh);
+            }
+        }
+        // the tile leaves by one bulk store
+        dev::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            dev::bulk_s2g_addr(reinterpret_cast<unsigned char *>(J.out) + first * 8u, stage, uint32_t(tile) * 8u);
+            dev::bulk_commit();
+        }
+        issued = true;
+    }
+    if (lane == 0 && issued) dev::bulk_wait_all();
+}
+
 // One work unit of a batch: edges [u * unit_edges, ...) of job unit_job[u].
 template <bool U64, int FMT, bool SMEM, bool LEVELS, int EPI, bool PRE>
 __device__ __forceinline__ void batch_unit(const Job &J, const Scramble &S, SharedKeys ks, uint32_t sblob,
@@ -969,9 +1080,13 @@ rmat_status plan_alias_launch(const rmat_table *t, const rmat_launch_config_t &w
     plan.tile = tile;
     plan.smem_bytes = need(smem_table, threads, tile);
     const int d4 = phase1_draws(t) == 4 ? 1 : 0;
-    plan.kernel = alias_kernel_table[d4][plan.fmt][u64][smem_table][levels]
-                                    [((t->flags & RMAT_UNDIRECTED) ? kEpiUndir : 0) | (t->scramble ? kEpiScr : 0)]();
+    const int epi = ((t->flags & RMAT_UNDIRECTED) ? kEpiUndir : 0) | (t->scramble ? kEpiScr : 0);
+    plan.kernel = alias_kernel_table[d4][plan.fmt][u64][smem_table][levels][epi]();
+    plan.fast_kernel = (d4 && plan.fmt == kCompact && !u64 && smem_table && !levels && epi == 0)
+                           ? reinterpret_cast<void *>(&k_alias_fast)
+                           : nullptr;
     cudaError_t e = set_smem_attr(plan.kernel, plan.smem_bytes);
+    if (e == cudaSuccess && plan.fast_kernel) e = set_smem_attr(plan.fast_kernel, plan.smem_bytes);
     if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan.kernel, threads, plan.smem_bytes);
@@ -1049,9 +1164,27 @@ rmat_status launch_alias(const rmat_table *t, const uint32_t *dblob, const Alias
     int tile = plan.tile;
     const uint64_t grid_warps = uint64_t(plan.sms) * plan.ctas_per_sm * warps;
     while (tile > 64 && tile % 64 == 0 && (count + tile - 1) / tile < grid_warps) tile /= 2;
+    const uint64_t max_ctas = uint64_t(plan.sms) * plan.ctas_per_sm;
+    // The whole tiles of an aligned output go to the contract-case kernel when
+    // the table allows it; the ragged tail (and every other case) to k_alias.
+    if (plan.fast_kernel && tile % 128 == 0 && count >= uint64_t(tile) &&
+        (reinterpret_cast<uintptr_t>(out) & 15u) == 0) {
+        const uint64_t nfull = count / uint64_t(tile);
+        Job F = J;
+        F.count = nfull * uint64_t(tile);
+        const unsigned grid = unsigned(std::max<uint64_t>(1, std::min((nfull + warps - 1) / warps, max_ctas)));
+        void *params[] = {&F, &tile};
+        cudaError_t e =
+            cudaLaunchKernel(plan.fast_kernel, dim3(grid), dim3(plan.threads), params, plan.smem_bytes, stream);
+        if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+        if (count == F.count) return RMAT_OK;
+        J.e0 += F.count;
+        J.count = count - F.count;
+        J.out = static_cast<unsigned char *>(out) + F.count * 8u;
+        count = J.count;
+    }
     const uint64_t ntiles = (count + tile - 1) / tile;
     const uint64_t want_ctas = (ntiles + warps - 1) / warps;
-    const uint64_t max_ctas = uint64_t(plan.sms) * plan.ctas_per_sm;
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want_ctas, max_ctas)));
     void *params[] = {&J, &S, &tile, &err};
     cudaError_t e = cudaLaunchKernel(plan.kernel, dim3(grid), dim3(plan.threads), params, plan.smem_bytes, stream);

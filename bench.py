@@ -35,13 +35,18 @@ WORKLOAD = ("R-MAT k=26 (n=2^26), m=2^30 edges (edge factor 16), a,b,c,d=0.57,0.
             "variable-length similar-probability paths, table bound 2^12 (4093 entries), "
             "Philox4x32-10 seed=1, u32 (row,col) pairs")
 FALLBACK_HBM_GBS = 6800.0
-# DRAM traffic of one full-size k_alias launch of this workload (2^30 edges), from
-# `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (1 pass) on the bench
-# command; valid only for the kernel sources whose hash is recorded with it.
-TRAFFIC = {"kernel_sha256_16": "b23a05095493de2d", "bytes_per_launch": 0.73e6 + 8.53e9}
+# DRAM traffic of the timed kernel (k_alias_fast) per 2^30-edge launch: the
+# read + write bytes of one m=2^28 launch (`ncu --metrics dram__bytes_read.sum,
+# dram__bytes_write.sum`, 1 pass, profiles/k_alias_fast_k26_m2p28_traffic.md)
+# scaled by the edges (x4); valid only for the kernel sources whose hash is
+# recorded with it.
+TRAFFIC = {"kernel_sha256_16": "0b212d8113454048", "bytes_per_launch": 4 * (968192 + 2085514752),
+           "source": "m=2^28 capture scaled x4 (profiles/k_alias_fast_k26_m2p28_traffic.md)"}
 # Warp instructions per edge of the same kernel (smsp__inst_executed.sum / 2^26 on
-# the m=2^26 `ncu --set full` capture of this workload), valid for the same hash.
-INSTR = {"kernel_sha256_16": "b23a05095493de2d", "warp_instr_per_edge": 309336748 / 2 ** 26}
+# the m=2^26 `ncu --set full` capture of this workload; ALU-pipe instructions from
+# smsp__inst_executed_pipe_alu.sum on the same case), valid for the same hash.
+INSTR = {"kernel_sha256_16": "0b212d8113454048", "warp_instr_per_edge": 293341562 / 2 ** 26,
+         "alu_warp_instr_per_edge": 71.1 / 32}
 KERNEL_SOURCES = ("paper_1905_03525_gb300/csrc/rmat_device.cuh", "paper_1905_03525_gb300/csrc/rmat_kernels.cu")
 
 
@@ -55,20 +60,25 @@ def kernel_hash() -> str:
 
 
 def issue_roofline(edges_per_s: float, sm_mhz: float):
-    """The bound the kernel actually meets, integer (ALU) instruction issue:
-    achieved warp instructions per second against SMs x 4 schedulers x the SM
-    clock sampled in the run.  `roofline` stays the HBM-write fraction that
-    the metric names."""
+    """The bound the kernel actually meets: its integer pipes.  The ALU pipe
+    (16 lanes per scheduler: half a warp instruction per clock, measured on
+    this GPU) carries the most work; `frac` is the achieved ALU warp
+    instructions per second against SMs x 4 schedulers x 0.5 x the SM clock
+    sampled in the run.  `issue_frac` compares all instructions with one per
+    scheduler per clock.  `roofline` stays the HBM-write fraction that the
+    metric names."""
     import torch
     if INSTR["kernel_sha256_16"] != kernel_hash() or not INSTR["warp_instr_per_edge"] or not sm_mhz:
         return None
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-    achieved = edges_per_s * INSTR["warp_instr_per_edge"]
-    peak = sms * 4 * sm_mhz * 1e6
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "warp-instr/s", "frac": achieved / peak,
+    issue_peak = sms * 4 * sm_mhz * 1e6
+    alu = edges_per_s * INSTR["alu_warp_instr_per_edge"]
+    return {"bound": "alu", "achieved": alu, "peak": 0.5 * issue_peak, "unit": "ALU warp-instr/s",
+            "frac": alu / (0.5 * issue_peak), "issue_frac": edges_per_s * INSTR["warp_instr_per_edge"] / issue_peak,
             "warp_instr_per_edge": INSTR["warp_instr_per_edge"],
-            "source": "smsp__inst_executed.sum of the m=2^26 ncu capture of the same kernel sources; "
-                      "peak = SMs x 4 schedulers x median SM clock of this run"}
+            "alu_warp_instr_per_edge": INSTR["alu_warp_instr_per_edge"],
+            "source": "smsp__inst_executed(_pipe_alu).sum of m=2^26 ncu captures of the same kernel sources; "
+                      "peak = SMs x 4 schedulers x 0.5 ALU instr/clock x median SM clock of this run"}
 
 
 def measured_traffic(log2m: int):
@@ -343,7 +353,8 @@ def run_ours(args):
                    "l2": "no flush: each step writes 8 GiB, far larger than the 126 MiB L2",
                    "parallelism": f"edge-range sharding x{world}, no collective"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": measured_traffic(args.log2m), "peak_source": f"{peak_src} hbm_gbs (copy)",
+                     "traffic": measured_traffic(args.log2m), "traffic_source": TRAFFIC["source"],
+                     "kernel": "k_alias_fast", "peak_source": f"{peak_src} hbm_gbs (copy)",
                      "algorithmic_bytes_per_launch": 8 * m, "avg_launch_ms": avg_launch_s * 1e3},
         "issue_roofline": issue_roofline(m / avg_launch_s, cs["sm_mhz"]),
         "cpu_baseline": cb,

@@ -350,12 +350,22 @@ void rmat_free_partition(rmat_partition *p);
  * the output of rmat_generate_partition); the first occurrence of every
  * (row, col) in array order is kept and the survivors are compacted to the
  * front in that order; *unique receives their number.  Synchronous on
- * `stream`; count <= 2^31; allocates and frees 45 to 77 bytes of device
- * scratch per edge (a hash table of 16-byte slots, a power of two at least
- * twice the edge count, and 13 bytes per edge).  Errors:
- * RMAT_ERR_INVALID_ARGUMENT (k, count, alignment), RMAT_ERR_OUT_OF_MEMORY,
- * RMAT_ERR_CUDA. */
+ * `stream`; count <= 2^31.  Device scratch of about 24 bytes per edge is
+ * allocated by the first call on a device and kept for later calls there
+ * (grown when a call needs more; rmat_dedup_release frees it); calls on one
+ * device take turns on it under a lock.  A hash bucket of more than 6144
+ * edges (possible only when few keys repeat many times) is done in a device
+ * table of 16-byte slots, a power of two at least twice that bucket, that the
+ * call allocates and frees.  Errors: RMAT_ERR_INVALID_ARGUMENT (k, count,
+ * alignment), RMAT_ERR_OUT_OF_MEMORY, RMAT_ERR_UNSUPPORTED (no current
+ * device), RMAT_ERR_CUDA. */
 rmat_status rmat_dedup_edges(void *edges, uint64_t count, int k, uint64_t *unique, rmat_stream_t stream);
+
+/* Free the scratch that rmat_dedup_edges keeps on the current device (no-op
+ * when it holds none, or when there is no device).  Not to be called while a
+ * rmat_dedup_edges call on that device is running in another thread: it
+ * waits for that call's lock.  Errors: RMAT_ERR_CUDA. */
+rmat_status rmat_dedup_release(void);
 
 /* ---------------------------------------------------------------------- */
 /* Serving: continuous batching of generation requests                     */

@@ -24,7 +24,7 @@ __all__ = [
     "rmat_generate_batch_noalloc", "rmat_batch_add_tile", "Partition", "rmat_partition_create",
     "rmat_partition_info", "rmat_partition_tiles", "rmat_generate_partition", "rmat_free_partition",
     "rmat_build_table_kron", "rmat_build_table_kron_fixed", "empty_edges_for", "rmat_build_table_gpu",
-    "rmat_dedup_edges", "rmat_selftest_bounded_wait",
+    "rmat_dedup_edges", "rmat_dedup_release", "rmat_selftest_bounded_wait",
 ]
 
 
@@ -370,6 +370,12 @@ def rmat_dedup_edges(edges, count: int, k: int, stream=None) -> int:
     n = ctypes.c_uint64()
     check(lib().rmat_dedup_edges(_ptr(edges), count, k, ctypes.byref(n), _stream(stream)))
     return n.value
+
+
+def rmat_dedup_release() -> None:
+    """Free the device scratch that rmat_dedup_edges keeps for later calls on
+    the current device."""
+    check(lib().rmat_dedup_release())
 
 
 def rmat_selftest_bounded_wait(limit: int = 4096) -> None:

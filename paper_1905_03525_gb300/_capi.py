@@ -90,6 +90,7 @@ SIGNATURES = [
     ("rmat_generate_partition", _st, [_vp, _vp, _vp]),
     ("rmat_free_partition", None, [_vp]),
     ("rmat_dedup_edges", _st, [_vp, _u64, _i32, _vp, _vp]),
+    ("rmat_dedup_release", _st, []),
     ("rmat_selftest_bounded_wait", _st, [_u32]),
     ("rmat_table_info", _st, [_vp, _vp]),
     ("rmat_table_group_info", _st, [_vp, _i32, _vp, _vp, _vp]),

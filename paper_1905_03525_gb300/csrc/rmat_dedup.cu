@@ -4,23 +4,37 @@
 //
 // The first occurrence of every (row, col), in the order of the input, stays;
 // the survivors are compacted to the front in that order, so the result is a
-// pure function of the input array.  Three passes over the edges:
-//   1. insert key = row * 2^k + col into an open-addressing hash table of
-//      16-byte slots {key, first index} (linear probing): one 128-bit CAS
-//      claims a free slot with the edge's key and index; an edge that finds
-//      its key already there lowers the slot's first index with atomicMin
-//      when its own index is smaller; each edge remembers its slot;
-//   2. an edge survives iff it holds its slot's first index: one flag byte
-//      per edge and per-chunk counts;
-//   3. exclusive scan of the chunk counts, then an ordered chunk-local
-//      compaction driven by the flags (sequential reads) into a second
-//      buffer, copied back.
-// The table has at least twice as many slots as edges; every probe loop is
-// bounded by the table size and reports an error instead of spinning.
+// pure function of the input array.  Two radix passes on a hash of the key
+// cut the edges into buckets small enough for one CTA's shared memory, and
+// every bucket is deduplicated there; nothing random touches device memory
+// but one bit per repeated edge:
+//   1. histogram of the level-1 digit, the top B1 bits of h = mix64(key),
+//      key = row * 2^k + col, and its exclusive scan on the device;
+//   2. scatter of {h, index} into the level-1 buckets, a tile at a time,
+//      staged in shared memory so that every run is written in one burst
+//      (mix64 is a bijection, so equal hashes mean equal edges and later
+//      passes need neither the key nor the hash function);
+//   3. when the edges need more than 2^B1 buckets, one CTA per level-1 bucket
+//      counts the next B2 bits of h, scans them and scatters its edges into
+//      its sub-buckets (a second buffer, staged the same way), for
+//      2^(B1+B2) buckets of at most ~2048 edges on average;
+//   4. one CTA per bucket: an open-addressing table in shared memory (64-bit
+//      CAS claims a slot for a key, 32-bit atomicMin keeps the smallest edge
+//      index of that key); every edge that is not its key's smallest index
+//      clears its bit in a survivor bitmap that starts all ones.  A bucket
+//      too large for shared memory (many copies of few keys) is listed and
+//      done afterwards in a device-memory table, one bucket after another;
+//   5. per-chunk survivor counts, one-block scan, ordered chunk-local
+//      compaction into a spare buffer, copied back.
+// The scratch (about 24 bytes per edge) is kept between calls.  Every probe
+// loop is bounded by its table's size and reports an error instead of
+// spinning.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
+#include <vector>
 
 #include "rmat_internal.h"
 #include "rmat_kernels.h"
@@ -28,14 +42,23 @@
 namespace rmat {
 namespace {
 
-constexpr uint64_t kEmpty = ~uint64_t(0);
+constexpr uint64_t kFree = ~uint64_t(0);           // fill of the overflow table: bucket number 0xFFFFFFFF
 constexpr int kBlock = 1024;
 constexpr int kPerThread = 4;                      // edges per thread in the compaction
-static_assert(kPerThread == 4, "k_dedup_count stores a thread's flags as one 4-byte word");
 constexpr uint64_t kChunk = uint64_t(kBlock) * kPerThread;
+constexpr int kL1MaxBits = 10;                     // level-1 buckets: at most 1024
+constexpr int kMaxBits = 20;                       // buckets in all: at most 2^20
+constexpr int kL2MaxBits = kMaxBits - kL1MaxBits;  // sub-buckets per level-1 bucket: at most 1024
+constexpr uint64_t kLocalTarget = 2048;            // mean edges per bucket, at most
+constexpr uint32_t kLocalMax = 6144;               // largest bucket done in shared memory
+constexpr uint32_t kLocalSlots = 8192;             // its table: load <= 0.75
+constexpr int kLocalThreads = 512;
+constexpr size_t kLocalSmem = size_t(kLocalSlots) * 12;  // keys and smallest indices
+static_assert((1 << kL2MaxBits) == kBlock, "one sub-bucket counter per thread of the split");
 
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
-    // splitmix64 finaliser (Steele, Lea, Flood 2014) as the hash
+    // splitmix64 finaliser (Steele, Lea, Flood 2014) as the hash; a bijection
+    // of 64-bit words
     x ^= x >> 30;
     x *= 0xBF58476D1CE4E5B9ull;
     x ^= x >> 27;
@@ -46,6 +69,317 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
 __device__ __forceinline__ uint64_t edge_key(const uint2 *e, uint64_t i, int k) {
     const uint2 v = e[i];
     return (uint64_t(v.x) << k) | v.y;
+}
+
+// The top `bits` bits of a hash (0 when bits = 0).
+__device__ __forceinline__ uint32_t top_bits(uint64_t h, int bits) { return bits ? uint32_t(h >> (64 - bits)) : 0u; }
+
+// Exclusive prefix sum over a block of kBlock threads, one value each; `ws`
+// holds 32 words.  Every thread of the block calls it.
+__device__ __forceinline__ uint32_t block_exclusive(uint32_t v, uint32_t *ws) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t y = ws[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += z;
+        }
+        ws[lane] = y;
+    }
+    __syncthreads();
+    return x - v + (warp ? ws[warp - 1] : 0u);
+}
+
+// 1. Level-1 bucket sizes: a block histogram in shared memory, added to `counts`.
+__global__ void __launch_bounds__(kBlock) k_dd_hist(const uint2 *edges, uint64_t n, int k, int bits,
+                                                    uint32_t *counts) {
+    __shared__ uint32_t h[1u << kL1MaxBits];
+    const uint32_t nb = 1u << bits;
+    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x)
+        atomicAdd(&h[top_bits(mix64(edge_key(edges, i, k)), bits)], 1u);
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
+        if (h[b]) atomicAdd(&counts[b], h[b]);
+}
+
+// 2. Level-1 scatter, one tile of kScatterTile edges at a time (persistent
+// blocks): every edge's bucket and rank within the tile come from
+// shared-memory counters; one atomic per bucket and tile reserves a run from
+// the bucket cursors; the tile is staged in shared memory sorted by bucket,
+// and written out so that consecutive threads write consecutive entries of a
+// run (a run is written in one burst, so L2 merges the partial lines at its
+// ends with the neighbouring runs instead of evicting them half written).
+constexpr int kScatterTile = 8192;
+constexpr int kScatterPer = kScatterTile / kBlock;
+constexpr size_t kScatterSmem = size_t(kScatterTile) * (8 + 4 + 2) + 3 * 4 * (size_t(1) << kL1MaxBits);
+static_assert((1 << kL1MaxBits) <= kBlock, "one bucket counter per thread of the scatter");
+__global__ void __launch_bounds__(kBlock, 1) k_dd_scatter(const uint2 *edges, uint64_t n, int k, int bits,
+                                                          uint32_t *cursor, uint64_t *bhash, uint32_t *bidx) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    auto *skey = reinterpret_cast<uint64_t *>(dsm);
+    auto *sidx = reinterpret_cast<uint32_t *>(dsm + size_t(kScatterTile) * 8);
+    auto *sdig = reinterpret_cast<uint16_t *>(dsm + size_t(kScatterTile) * 12);
+    auto *cnt = reinterpret_cast<uint32_t *>(dsm + size_t(kScatterTile) * 14);
+    uint32_t *off = cnt + (1u << kL1MaxBits);
+    uint32_t *gbase = off + (1u << kL1MaxBits);
+    __shared__ uint32_t ws[32];
+    const uint32_t t = threadIdx.x;
+    const uint64_t tiles = (n + kScatterTile - 1) / kScatterTile;
+    cnt[t] = 0;
+    __syncthreads();
+    for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const uint64_t t0 = tile * kScatterTile;
+        const uint32_t tn = uint32_t(min(uint64_t(kScatterTile), n - t0));
+        uint64_t h[kScatterPer];
+        uint32_t dig[kScatterPer], rank[kScatterPer];
+#pragma unroll
+        for (int u = 0; u < kScatterPer; ++u) {
+            const uint32_t i = u * kBlock + t;
+            h[u] = i < tn ? edge_key(edges, t0 + i, k) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kScatterPer; ++u) {
+            h[u] = mix64(h[u]);
+            dig[u] = top_bits(h[u], bits);
+            rank[u] = u * kBlock + t < tn ? atomicAdd(&cnt[dig[u]], 1u) : 0u;
+        }
+        __syncthreads();
+        const uint32_t c = cnt[t];  // 0 past the last bucket
+        const uint32_t ex = block_exclusive(c, ws);
+        off[t] = ex;
+        const uint32_t gb = c ? atomicAdd(&cursor[t], c) : 0u;  // used after the staging
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kScatterPer; ++u) {
+            const uint32_t i = u * kBlock + t;
+            if (i >= tn) continue;
+            const uint32_t p = off[dig[u]] + rank[u];
+            skey[p] = h[u];
+            sidx[p] = uint32_t(t0 + i);
+            sdig[p] = uint16_t(dig[u]);
+        }
+        gbase[t] = gb;
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kScatterPer; ++u) {
+            const uint32_t p = u * kBlock + t;
+            if (p >= tn) continue;
+            const uint32_t d = sdig[p];
+            const uint32_t g = gbase[d] + (p - off[d]);
+            bhash[g] = skey[p];
+            bidx[g] = sidx[p];
+        }
+        cnt[t] = 0;
+        __syncthreads();
+    }
+}
+
+// 3. Level-2 split of level-1 bucket b = blockIdx.x, entries [lo1[b], hi1[b])
+// of (akey, aidx): counts of the digit (h >> (64 - B)) mod 2^B2 (the bits
+// below the level-1 digit) over the bucket, their scan, the start of every
+// sub-bucket in sub_start[b * 2^B2 + d]; then the bucket a tile of
+// kSplitTile entries at a time, staged in shared memory sorted by sub-bucket
+// as in the level-1 scatter, into (bkey, bidx).  The block owns its bucket, so
+// the sub-bucket cursors live in shared memory.
+constexpr int kSplitTile = 4096;
+constexpr int kSplitPer = kSplitTile / kBlock;
+constexpr size_t kSplitSmem = size_t(kSplitTile) * (8 + 4 + 2) + 4 * 4 * (size_t(1) << kL2MaxBits);
+__global__ void __launch_bounds__(kBlock, 1) k_dd_split(const uint64_t *akey, const uint32_t *aidx, const uint32_t *lo1,
+                                                        const uint32_t *hi1, int B, int B2, uint64_t *bkey,
+                                                        uint32_t *bidx, uint32_t *sub_start) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    auto *skey = reinterpret_cast<uint64_t *>(dsm);
+    auto *sidx = reinterpret_cast<uint32_t *>(dsm + size_t(kSplitTile) * 8);
+    auto *sdig = reinterpret_cast<uint16_t *>(dsm + size_t(kSplitTile) * 12);
+    auto *cnt = reinterpret_cast<uint32_t *>(dsm + size_t(kSplitTile) * 14);
+    uint32_t *off = cnt + (1u << kL2MaxBits);
+    uint32_t *base = off + (1u << kL2MaxBits);
+    uint32_t *cur = base + (1u << kL2MaxBits);
+    __shared__ uint32_t ws[32];
+    const uint32_t t = threadIdx.x;
+    const uint32_t b = blockIdx.x, lo = lo1[b], hi = hi1[b];
+    const uint32_t nd = 1u << B2, dmask = nd - 1;
+    const int sh = 64 - B;
+    auto digit = [&](uint64_t h) { return uint32_t(h >> sh) & dmask; };
+    cnt[t] = 0;
+    __syncthreads();
+    for (uint32_t j0 = lo + t; j0 < hi; j0 += 4 * kBlock) {
+        uint64_t key[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t j = j0 + u * kBlock;
+            key[u] = j < hi ? akey[j] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (j0 + u * kBlock < hi) atomicAdd(&cnt[digit(key[u])], 1u);
+    }
+    __syncthreads();
+    {
+        const uint32_t v = t < nd ? cnt[t] : 0u;
+        const uint32_t ex = block_exclusive(v, ws);
+        if (t < nd) sub_start[(b << B2) + t] = lo + ex;
+        cur[t] = lo + ex;
+        cnt[t] = 0;
+    }
+    __syncthreads();
+    uint64_t key[kSplitPer];
+    uint32_t idx[kSplitPer];
+    auto load = [&](uint32_t j0) {
+        const uint32_t tn = j0 < hi ? min(uint32_t(kSplitTile), hi - j0) : 0u;
+#pragma unroll
+        for (int u = 0; u < kSplitPer; ++u) {
+            const uint32_t i = u * kBlock + t;
+            key[u] = i < tn ? akey[j0 + i] : 0;
+            idx[u] = i < tn ? aidx[j0 + i] : 0;
+        }
+    };
+    load(lo);
+    for (uint32_t j0 = lo; j0 < hi; j0 += kSplitTile) {
+        const uint32_t tn = min(uint32_t(kSplitTile), hi - j0);
+        uint32_t dig[kSplitPer], rank[kSplitPer];
+#pragma unroll
+        for (int u = 0; u < kSplitPer; ++u) {
+            dig[u] = digit(key[u]);
+            rank[u] = u * kBlock + t < tn ? atomicAdd(&cnt[dig[u]], 1u) : 0u;
+        }
+        __syncthreads();
+        const uint32_t c = cnt[t];  // 0 past the last sub-bucket
+        off[t] = block_exclusive(c, ws);
+        base[t] = cur[t];
+        cur[t] += c;
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kSplitPer; ++u) {
+            if (u * kBlock + t >= tn) continue;
+            const uint32_t p = off[dig[u]] + rank[u];
+            skey[p] = key[u];
+            sidx[p] = idx[u];
+            sdig[p] = uint16_t(dig[u]);
+        }
+        load(j0 + kSplitTile);
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kSplitPer; ++u) {
+            const uint32_t p = u * kBlock + t;
+            if (p >= tn) continue;
+            const uint32_t d = sdig[p];
+            const uint32_t g = base[d] + (p - off[d]);
+            bkey[g] = skey[p];
+            bidx[g] = sidx[p];
+        }
+        cnt[t] = 0;
+        __syncthreads();
+    }
+}
+
+// 4. Bucket s = blockIdx.x, entries [starts[s], starts[s + 1]) (n for the
+// last), deduplicated in shared memory.  The table has T slots, a power of two
+// at least twice the bucket (at most kLocalSlots, so a bucket of at most
+// kLocalMax edges always finds a free slot within T probes).  A key's slot
+// never changes once claimed, and every copy of the key probes the same
+// sequence, so all copies meet in one slot; each lowers the slot's index to
+// its own, and after the barrier every copy that does not hold the minimum
+// clears its survivor bit.  The table holds hashes (equal hashes, equal
+// edges); an empty slot holds a value whose top B bits are not s, so no hash
+// of this bucket.  A thread keeps its edges' indices and slots in registers
+// (at most kLocalBatches x 4 edges), and the first edges' loads are in flight
+// while the table is cleared.  A larger bucket goes to the overflow list
+// (ovf[0] = how many, ovf[1 + i] = bucket).
+constexpr int kLocalBatches = int(kLocalMax / (4 * kLocalThreads));
+static_assert(kLocalBatches * 4 * kLocalThreads == int(kLocalMax), "whole batches of four edges per thread");
+__global__ void __launch_bounds__(kLocalThreads, 2) k_dd_local(const uint64_t *hash, const uint32_t *idx,
+                                                               const uint32_t *starts, uint32_t nsub, int B, uint32_t n,
+                                                               uint32_t *bitmap, uint32_t *ovf, unsigned *err) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    auto *skey = reinterpret_cast<unsigned long long *>(dsm);
+    auto *sidx = reinterpret_cast<uint32_t *>(dsm + size_t(kLocalSlots) * 8);
+    const uint32_t s = blockIdx.x;
+    const uint32_t lo = starts[s], hi = s + 1 < nsub ? starts[s + 1] : n;
+    const uint32_t cnt = hi - lo;
+    if (cnt <= 1) return;  // a lone edge is a first occurrence
+    if (cnt > kLocalMax) {
+        if (threadIdx.x == 0) ovf[1 + atomicAdd(ovf, 1u)] = s;
+        return;
+    }
+    uint32_t T = 64;
+    while (T < 2 * cnt && T < kLocalSlots) T <<= 1;
+    const uint32_t tmask = T - 1;
+    const int batches = int((cnt + 4 * kLocalThreads - 1) / (4 * kLocalThreads));
+    const unsigned long long empty = uint64_t(s ^ 1u) << (64 - B);  // B >= 1
+    uint64_t kk[4];
+    uint32_t id[4 * kLocalBatches], sl[4 * kLocalBatches];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const uint32_t r = threadIdx.x + u * kLocalThreads;
+        kk[u] = r < cnt ? hash[lo + r] : 0;
+        id[u] = r < cnt ? idx[lo + r] : 0;
+    }
+    for (uint32_t i = threadIdx.x; i < T; i += kLocalThreads) {
+        skey[i] = empty;
+        sidx[i] = ~0u;
+    }
+    __syncthreads();
+    volatile unsigned long long *vkey = skey;
+    bool lost = false;
+#pragma unroll
+    for (int bt = 0; bt < kLocalBatches; ++bt) {
+        if (bt >= batches) break;
+        if (bt > 0) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t r = threadIdx.x + (bt * 4 + u) * kLocalThreads;
+                kk[u] = r < cnt ? hash[lo + r] : 0;
+                id[bt * 4 + u] = r < cnt ? idx[lo + r] : 0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = bt * 4 + u;
+            sl[e] = 0;
+            if (threadIdx.x + e * kLocalThreads >= cnt) continue;
+            uint32_t h = uint32_t(kk[u]) & tmask;
+            bool placed = false;
+            for (uint32_t probe = 0; probe < T; ++probe) {
+                unsigned long long c = vkey[h];
+                if (c == empty) c = atomicCAS(&skey[h], empty, (unsigned long long)kk[u]);
+                if (c == empty || c == kk[u]) {
+                    placed = true;
+                    break;
+                }
+                h = (h + 1) & tmask;
+            }
+            if (!placed) {  // never expected: T exceeds the bucket's size
+                lost = true;
+                h = 0;
+            }
+            atomicMin(&sidx[h], id[e]);
+            sl[e] = h;
+        }
+    }
+    if (lost) atomicOr(err, 8u);
+    __syncthreads();
+#pragma unroll
+    for (int bt = 0; bt < kLocalBatches; ++bt) {
+        if (bt >= batches) break;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = bt * 4 + u;
+            if (threadIdx.x + e * kLocalThreads >= cnt) continue;
+            if (sidx[sl[e]] != id[e]) atomicAnd(bitmap + (id[e] >> 5), ~(1u << (id[e] & 31)));
+        }
+    }
 }
 
 // 128-bit compare-and-swap (PTX atom.cas.b128, sm_90 and later) on the
@@ -63,53 +397,89 @@ __device__ __forceinline__ void cas128(unsigned long long *addr, uint64_t cmp_lo
         : "memory");
 }
 
-// Slot h of the table: tab[2h] = key (kEmpty when free), tab[2h + 1] = the
-// smallest index of an edge with that key (all ones while free).  A slot
-// leaves the free state once, by the CAS that writes both words; after that
-// only its index word changes, by atomicMin.
-__global__ void k_dedup_insert(const uint2 *edges, uint64_t n, int k, unsigned long long *tab, uint64_t mask,
-                               uint32_t *slot_of, unsigned *err) {
-    for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x) {
-        const uint64_t key = edge_key(edges, i, k);
-        uint64_t h = mix64(key) & mask;
-        bool placed = false;
-        for (uint64_t probe = 0; probe <= mask; ++probe) {  // at most one pass over the table
-            uint64_t old_key, old_first;
-            cas128(tab + 2 * h, kEmpty, kEmpty, key, i, old_key, old_first);
-            if (old_key == kEmpty || old_key == key) {
-                if (old_key == key && i < old_first) atomicMin(tab + 2 * h + 1, (unsigned long long)i);
-                slot_of[i] = uint32_t(h);
-                placed = true;
-                break;
+// 4'. A bucket too large for shared memory, entries [begin, begin + count):
+// insert into a device-memory table of 16-byte slots {hash, (bucket << 32) |
+// smallest index}; a slot is told free by its second word only.  The table is shared by the overflow buckets, one after
+// another: a slot holding another bucket's number counts as free.  A CAS only
+// ever succeeds on a slot that does not carry this bucket's number, and
+// atomicMin only ever targets slots that do, so no successful CAS overlaps a
+// minimum on the same slot.  Every decision rests on a CAS's 16-byte
+// snapshot, except that a plain read showing this bucket and this key is
+// final (such a slot's key never changes within the launch).
+__global__ void __launch_bounds__(256) k_dd_insert(const uint64_t *bkey, const uint32_t *bidx, uint64_t begin,
+                                                   uint32_t count, unsigned long long *tab, uint64_t mask,
+                                                   uint32_t bucket, unsigned *err) {
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x) {
+        const uint64_t key = bkey[begin + j];
+        const uint64_t mine = (uint64_t(bucket) << 32) | bidx[begin + j];
+        uint64_t h = key & mask;  // `key` is the edge's hash
+        bool placed = false, lost = false;
+        for (uint64_t probe = 0; probe <= mask && !placed && !lost; ++probe) {
+            unsigned long long *slot = tab + 2 * h;
+            uint64_t ek = slot[0], ew = slot[1];  // a guess; the CAS returns the truth
+            bool next = false;
+            for (int tries = 0; tries < 64 && !placed && !next; ++tries) {
+                uint64_t gk, gw;
+                if ((ew >> 32) == bucket) {
+                    if (ek == key) {
+                        if (mine < ew) atomicMin(slot + 1, (unsigned long long)mine);
+                        placed = true;
+                        break;
+                    }
+                    // another key of this bucket: confirm with a CAS that cannot
+                    // succeed on a slot of this bucket
+                    cas128(slot, kFree, kFree, key, mine, gk, gw);
+                    if (gk == kFree && gw == kFree) placed = true;
+                    else if (gk == ek && gw == ew) next = true;
+                } else {
+                    cas128(slot, ek, ew, key, mine, gk, gw);
+                    if (gk == ek && gw == ew) placed = true;
+                }
+                ek = gk;
+                ew = gw;
             }
+            if (!placed && !next) lost = true;  // the slot kept changing (never expected)
             h = (h + 1) & mask;
         }
         if (!placed) atomicOr(err, 2u);
     }
 }
 
-// Survivor flags of chunk `c` (kChunk edges, thread t holds edges
-// c*kChunk + t*kPerThread + j; one byte per edge) and the chunk's count.
-__global__ void __launch_bounds__(kBlock) k_dedup_count(uint64_t n, const uint32_t *slot_of,
-                                                        const unsigned long long *tab, uint8_t *flag,
-                                                        uint32_t *chunk_count) {
-    __shared__ uint32_t warp_sum[kBlock / 32];
-    const uint64_t base = blockIdx.x * kChunk + uint64_t(threadIdx.x) * kPerThread;
-    uint32_t c = 0, bits = 0;
-#pragma unroll
-    for (int j = 0; j < kPerThread; ++j) {
-        const uint64_t i = base + j;
-        if (i < n && tab[2 * uint64_t(slot_of[i]) + 1] == i) {
-            ++c;
-            bits |= 1u << (8 * j);
+// 4''. After k_dd_insert of the same bucket: every edge whose index is not its
+// key's smallest clears its survivor bit.
+__global__ void __launch_bounds__(256) k_dd_clear(const uint64_t *bkey, const uint32_t *bidx, uint64_t begin,
+                                                  uint32_t count, const unsigned long long *tab, uint64_t mask,
+                                                  uint32_t bucket, uint32_t *bitmap, unsigned *err) {
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x) {
+        const uint64_t key = bkey[begin + j];
+        const uint32_t idx = bidx[begin + j];
+        uint64_t h = key & mask;
+        bool found = false;
+        for (uint64_t probe = 0; probe <= mask; ++probe) {
+            const uint64_t k0 = tab[2 * h], w = tab[2 * h + 1];
+            if ((w >> 32) == bucket && k0 == key) {
+                if (uint32_t(w) != idx) atomicAnd(bitmap + (idx >> 5), ~(1u << (idx & 31)));
+                found = true;
+                break;
+            }
+            h = (h + 1) & mask;
         }
+        if (!found) atomicOr(err, 4u);
     }
-    if (base + kPerThread <= n) {
-        *reinterpret_cast<uint32_t *>(flag + base) = bits;  // kPerThread == 4 flag bytes
-    } else {
-#pragma unroll
-        for (int j = 0; j < kPerThread; ++j)
-            if (base + j < n) flag[base + j] = uint8_t(bits >> (8 * j));
+}
+
+// 5a. Survivors of chunk `c` (kChunk edges: one bitmap word per thread; bits
+// at or past n are masked off).
+constexpr int kCountThreads = int(kChunk / 32);
+__global__ void __launch_bounds__(kCountThreads) k_dd_count(uint64_t n, const uint32_t *bitmap,
+                                                            uint32_t *chunk_count) {
+    __shared__ uint32_t warp_sum[kCountThreads / 32];
+    const uint64_t first = blockIdx.x * kChunk + uint64_t(threadIdx.x) * 32;
+    uint32_t c = 0;
+    if (first < n) {
+        uint32_t w = bitmap[first >> 5];
+        if (n - first < 32) w &= (1u << (n - first)) - 1u;
+        c = __popc(w);
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
@@ -117,12 +487,13 @@ __global__ void __launch_bounds__(kBlock) k_dedup_count(uint64_t n, const uint32
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t t = 0;
-        for (int w = 0; w < kBlock / 32; ++w) t += warp_sum[w];
+        for (int w = 0; w < kCountThreads / 32; ++w) t += warp_sum[w];
         chunk_count[blockIdx.x] = t;
     }
 }
 
-// Exclusive scan of the chunk counts in place (one block; chunks up to ~2^22).
+// Exclusive scan of `counts` in place (one block; up to ~2^22 entries); the
+// sum goes to *total.
 __global__ void __launch_bounds__(kBlock) k_dedup_scan(uint32_t *counts, uint64_t chunks, unsigned long long *total) {
     __shared__ uint32_t sm[kBlock / 32];
     __shared__ unsigned long long carry;
@@ -159,44 +530,35 @@ __global__ void __launch_bounds__(kBlock) k_dedup_scan(uint32_t *counts, uint64_
     if (threadIdx.x == 0) *total = carry;
 }
 
-// Ordered compaction of chunk `c` to dst starting at offsets[c].
-__global__ void __launch_bounds__(kBlock) k_dedup_compact(const uint2 *edges, uint64_t n, const uint8_t *flag,
-                                                          const uint32_t *offsets, uint2 *dst) {
-    __shared__ uint32_t warp_base[kBlock / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// 5c. Ordered compaction of chunk `c` to dst starting at offsets[c]: thread
+// t keeps the survivors among edges c * kChunk + 4t .. + 3 (one nibble of the
+// bitmap, bits at or past n masked off), ranked by a block prefix sum.
+__global__ void __launch_bounds__(kBlock) k_dd_compact(const uint2 *edges, uint64_t n, const uint32_t *bitmap,
+                                                       const uint32_t *offsets, uint2 *dst) {
+    static_assert(kPerThread == 4, "a thread takes one nibble of a bitmap word");
+    __shared__ uint32_t ws[32];
     const uint64_t base = blockIdx.x * kChunk + uint64_t(threadIdx.x) * kPerThread;
-    uint32_t keep = 0, c = 0;
-#pragma unroll
-    for (int j = 0; j < kPerThread; ++j) {
-        const uint64_t i = base + j;
-        if (i < n && flag[i]) {
-            keep |= 1u << j;
-            ++c;
-        }
+    uint32_t keep = 0;
+    if (base < n) {
+        keep = (bitmap[base >> 5] >> (base & 31)) & 0xFu;
+        if (n - base < 4) keep &= (1u << (n - base)) - 1u;
     }
-    uint32_t x = c;  // inclusive scan over the warp, then over the warps
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_base[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t y = warp_base[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
-            if (lane >= o) y += z;
-        }
-        warp_base[lane] = y;
-    }
-    __syncthreads();
-    uint64_t out = uint64_t(offsets[blockIdx.x]) + (x - c) + (warp ? warp_base[warp - 1] : 0u);
+    const uint32_t c = __popc(keep);
+    uint64_t out = uint64_t(offsets[blockIdx.x]) + block_exclusive(c, ws);
 #pragma unroll
     for (int j = 0; j < kPerThread; ++j)
         if (keep & (1u << j)) dst[out++] = edges[base + j];
 }
+
+// Scratch kept between calls, per device; the mutex also serialises calls on
+// one device (they share the buffer).
+constexpr int kMaxDevices = 64;
+struct Scratch {
+    std::mutex mu;
+    unsigned char *ptr = nullptr;
+    size_t bytes = 0;
+};
+Scratch g_scratch[kMaxDevices];
 
 }  // namespace
 }  // namespace rmat
@@ -215,41 +577,152 @@ extern "C" rmat_status rmat_dedup_edges(void *edges, uint64_t count, int k, uint
     if (count > (uint64_t(1) << 31)) return fail(RMAT_ERR_INVALID_ARGUMENT, "at most 2^31 edges per call");
     DeviceProps props;
     if (rmat_status st = device_props(props)) return st;
-    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-
-    uint64_t slots = 1;
-    while (slots < 2 * count) slots <<= 1;
-    const uint64_t chunks = (count + kChunk - 1) / kChunk;
-    // scratch: the table (key, first index) per slot, slot per edge, flag
-    // byte per edge, chunk counts, the compacted copy, the total and an error
-    // word
-    const size_t off_slot = slots * 16;
-    const size_t off_flag = off_slot + ((count * 4 + 255) & ~size_t(255));
-    const size_t off_cnt = off_flag + ((count + 255) & ~size_t(255));
-    const size_t off_dst = off_cnt + ((chunks * 4 + 255) & ~size_t(255));
-    const size_t off_tot = off_dst + count * 8;
-    const size_t bytes = off_tot + 16;
-    unsigned char *scratch = nullptr;
-    if (cudaMalloc(&scratch, bytes) != cudaSuccess) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
-        return fail(RMAT_ERR_OUT_OF_MEMORY, "device scratch for duplicate removal");
+        return fail(RMAT_ERR_UNSUPPORTED, "duplicate removal: no usable current device");
     }
-    auto *tab = reinterpret_cast<unsigned long long *>(scratch);
-    auto *slot_of = reinterpret_cast<uint32_t *>(scratch + off_slot);
-    auto *flag = reinterpret_cast<uint8_t *>(scratch + off_flag);
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    auto cuda_fail = [](const char *what, cudaError_t e) {
+        return fail(RMAT_ERR_CUDA, std::string("duplicate removal, ") + what + ": " + cudaGetErrorString(e));
+    };
+
+    // B bits of buckets (mean size at most kLocalTarget), B1 of them at level 1
+    int B = 1;  // at least two buckets: an empty local slot is marked by the other bucket's number
+    while (B < kMaxBits && (count >> B) > kLocalTarget) ++B;
+    const int B1 = std::min(B, kL1MaxBits), B2 = B - B1;
+    const uint32_t nb1 = 1u << B1, nsub = 1u << B;
+    const uint32_t n = uint32_t(count);
+    const uint64_t chunks = (count + kChunk - 1) / kChunk;
+    const uint64_t words = (count + 31) / 32;
+    // scratch: level-1 starts and cursors, sub-bucket starts, the overflow
+    // list, two {key, index} buffers, the survivor bitmap, chunk counts, the
+    // total and an error word
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t off_cursor = up(4 * size_t(nb1));
+    const size_t off_sub = off_cursor + up(4 * size_t(nb1));
+    const size_t off_ovf = off_sub + up(4 * size_t(nsub));
+    const size_t off_akey = off_ovf + up(4 * (size_t(nsub) + 1));
+    const size_t off_bkey = off_akey + up(8 * count);
+    const size_t off_aidx = off_bkey + up(8 * count);
+    const size_t off_bidx = off_aidx + up(4 * count);
+    const size_t off_bits = off_bidx + up(4 * count);
+    const size_t off_cnt = off_bits + up(4 * words);
+    const size_t off_tot = off_cnt + up(4 * chunks);
+    const size_t bytes = off_tot + 256;
+
+    Scratch &sc = g_scratch[dev];
+    std::lock_guard<std::mutex> lock(sc.mu);
+    if (sc.bytes < bytes) {
+        if (sc.ptr) cudaFree(sc.ptr);
+        sc.ptr = nullptr;
+        sc.bytes = 0;
+        if (cudaMalloc(&sc.ptr, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            sc.ptr = nullptr;
+            return fail(RMAT_ERR_OUT_OF_MEMORY, "device scratch for duplicate removal");
+        }
+        sc.bytes = bytes;
+    }
+    unsigned char *scratch = sc.ptr;
+    unsigned long long *tab = nullptr;  // overflow table, only when some bucket needs it
+    auto done = [&](rmat_status st) {
+        cudaStreamSynchronize(stream);
+        if (tab) cudaFree(tab);
+        return st;
+    };
+    auto *start1 = reinterpret_cast<uint32_t *>(scratch);
+    auto *cursor = reinterpret_cast<uint32_t *>(scratch + off_cursor);
+    auto *sub = reinterpret_cast<uint32_t *>(scratch + off_sub);
+    auto *ovf = reinterpret_cast<uint32_t *>(scratch + off_ovf);
+    auto *akey = reinterpret_cast<uint64_t *>(scratch + off_akey);
+    auto *bkey = reinterpret_cast<uint64_t *>(scratch + off_bkey);
+    auto *aidx = reinterpret_cast<uint32_t *>(scratch + off_aidx);
+    auto *bidx = reinterpret_cast<uint32_t *>(scratch + off_bidx);
+    auto *bitmap = reinterpret_cast<uint32_t *>(scratch + off_bits);
     auto *cnt = reinterpret_cast<uint32_t *>(scratch + off_cnt);
-    auto *dst = reinterpret_cast<uint2 *>(scratch + off_dst);
     auto *total = reinterpret_cast<unsigned long long *>(scratch + off_tot);
     auto *err = reinterpret_cast<unsigned *>(scratch + off_tot + 8);
     const uint2 *src = static_cast<const uint2 *>(edges);
-    const int grid = props.sms * 8;
-    cudaError_t e = cudaMemsetAsync(tab, 0xFF, slots * 16, stream);  // kEmpty keys, first = max
+
+    // 1-2. level-1 sizes, starts (scan on the device), scatter
+    cudaError_t e = cudaMemsetAsync(start1, 0, 4 * size_t(nb1), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 4, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ovf, 0, 4, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bitmap, 0xFF, 4 * words, stream);  // every edge survives until cleared
     if (e == cudaSuccess) {
-        k_dedup_insert<<<grid, 256, 0, stream>>>(src, count, k, tab, slots - 1, slot_of, err);
-        k_dedup_count<<<unsigned(chunks), kBlock, 0, stream>>>(count, slot_of, tab, flag, cnt);
+        k_dd_hist<<<props.sms * 2, kBlock, 0, stream>>>(src, count, k, B1, start1);
+        k_dedup_scan<<<1, kBlock, 0, stream>>>(start1, nb1, total);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cursor, start1, 4 * size_t(nb1), cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_dd_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kScatterSmem));
+    if (e == cudaSuccess) {
+        const uint64_t tiles = (count + kScatterTile - 1) / kScatterTile;
+        const unsigned sgrid = unsigned(std::min<uint64_t>(tiles, uint64_t(props.sms)));
+        k_dd_scatter<<<sgrid, kBlock, kScatterSmem, stream>>>(src, count, k, B1, cursor, akey, aidx);
+        e = cudaGetLastError();
+    }
+    // 3. level-2 split (cursor[b] now ends level-1 bucket b)
+    const uint64_t *lkey = akey;
+    const uint32_t *lidx = aidx, *starts = start1;
+    uint2 *dst = reinterpret_cast<uint2 *>(bkey);
+    if (e == cudaSuccess && B2 > 0)
+        e = cudaFuncSetAttribute(k_dd_split, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSplitSmem));
+    if (e == cudaSuccess && B2 > 0) {
+        k_dd_split<<<nb1, kBlock, kSplitSmem, stream>>>(akey, aidx, start1, cursor, B, B2, bkey, bidx, sub);
+        e = cudaGetLastError();
+        lkey = bkey;
+        lidx = bidx;
+        starts = sub;
+        dst = reinterpret_cast<uint2 *>(akey);
+    }
+    // 4. buckets in shared memory
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_dd_local, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kLocalSmem));
+    if (e == cudaSuccess) {
+        k_dd_local<<<nsub, kLocalThreads, kLocalSmem, stream>>>(lkey, lidx, starts, nsub, B, n, bitmap, ovf, err);
+        e = cudaGetLastError();
+    }
+    uint32_t novf = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&novf, ovf, 4, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return done(cuda_fail("partition", e));
+    // 4'. buckets too large for shared memory, one after another in one table
+    if (novf) {
+        std::vector<uint32_t> list(novf), hs(nsub);
+        e = cudaMemcpyAsync(list.data(), ovf + 1, 4 * size_t(novf), cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), starts, 4 * size_t(nsub), cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return done(cuda_fail("overflow list", e));
+        std::sort(list.begin(), list.end());
+        auto size_of = [&](uint32_t s) { return (s + 1 < nsub ? hs[s + 1] : n) - hs[s]; };
+        uint64_t largest = 1;
+        for (uint32_t s : list) largest = std::max<uint64_t>(largest, size_of(s));
+        uint64_t slots = 1;
+        while (slots < 2 * largest) slots <<= 1;
+        if (cudaMalloc(&tab, slots * 16) != cudaSuccess) {
+            cudaGetLastError();
+            tab = nullptr;
+            return done(fail(RMAT_ERR_OUT_OF_MEMORY, "device hash table for duplicate removal"));
+        }
+        e = cudaMemsetAsync(tab, 0xFF, slots * 16, stream);  // no slot belongs to a bucket
+        for (uint32_t s : list) {
+            if (e != cudaSuccess) break;
+            const uint32_t c = size_of(s);
+            const unsigned g = unsigned(std::min<uint64_t>((c + 255) / 256, uint64_t(props.sms) * 8));
+            k_dd_insert<<<g, 256, 0, stream>>>(lkey, lidx, hs[s], c, tab, slots - 1, s, err);
+            k_dd_clear<<<g, 256, 0, stream>>>(lkey, lidx, hs[s], c, tab, slots - 1, s, bitmap, err);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) return done(cuda_fail("overflow buckets", e));
+    }
+    // 5. ordered compaction from the bitmap
+    if (e == cudaSuccess) {
+        k_dd_count<<<unsigned(chunks), kCountThreads, 0, stream>>>(count, bitmap, cnt);
         k_dedup_scan<<<1, kBlock, 0, stream>>>(cnt, chunks, total);
-        k_dedup_compact<<<unsigned(chunks), kBlock, 0, stream>>>(src, count, flag, cnt, dst);
+        k_dd_compact<<<unsigned(chunks), kBlock, 0, stream>>>(src, count, bitmap, cnt, dst);
         e = cudaGetLastError();
     }
     unsigned long long host_total = 0;
@@ -260,9 +733,27 @@ extern "C" rmat_status rmat_dedup_edges(void *edges, uint64_t count, int k, uint
     if (e == cudaSuccess && !host_err && host_total)
         e = cudaMemcpyAsync(edges, dst, host_total * 8, cudaMemcpyDeviceToDevice, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    cudaFree(scratch);
-    if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("duplicate removal: ") + cudaGetErrorString(e));
-    if (host_err) return fail(RMAT_ERR_CUDA, "duplicate removal: hash table full (internal error)");
+    if (e != cudaSuccess) return done(cuda_fail("kernels", e));
+    if (host_err) return done(fail(RMAT_ERR_CUDA, "duplicate removal: hash table full (internal error)"));
     *unique = host_total;
+    return done(RMAT_OK);
+}
+
+extern "C" rmat_status rmat_dedup_release(void) {
+    clear_error();
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return RMAT_OK;  // no device, nothing held
+    }
+    Scratch &sc = g_scratch[dev];
+    std::lock_guard<std::mutex> lock(sc.mu);
+    if (sc.ptr) {
+        const cudaError_t e = cudaFree(sc.ptr);
+        sc.ptr = nullptr;
+        sc.bytes = 0;
+        if (e != cudaSuccess)
+            return fail(RMAT_ERR_CUDA, std::string("cudaFree(dedup scratch): ") + cudaGetErrorString(e));
+    }
     return RMAT_OK;
 }

@@ -328,6 +328,7 @@ def test_dedup_host_checks():
     with pytest.raises(rm.RmatError):
         rm.rmat_dedup_edges(8, 10, 32)        # k above 31
     assert rm.rmat_dedup_edges(8, 0, 20) == 0  # nothing to do, no device needed
+    rm.rmat_dedup_release()                    # holds nothing: a no-op
 
 
 def test_selftest_argument_check():

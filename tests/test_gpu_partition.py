@@ -130,7 +130,8 @@ def _dedup_gpu(out, n, k):
     return u, pairs(out[:u], k)
 
 
-@pytest.mark.parametrize("k,m", [(8, 200_000), (12, 100_003), (3, 5000), (20, 1 << 20)])
+@pytest.mark.parametrize("k,m", [(8, 200_000), (12, 100_003), (3, 5000), (20, 1 << 20),
+                                 (12, (3 << 21) + 7), (24, (1 << 23) + 3)])   # the last two: two levels of buckets
 def test_dedup_keeps_first_occurrences(k, m):
     t = rm.rmat_build_table(*G500, k, 256)
     ot = oracle.Table.variable(*G500, k, 256)
@@ -140,6 +141,25 @@ def test_dedup_keeps_first_occurrences(k, m):
     ref = oracle.dedup_first(*oracle.generate([ot], k, 3, 0, m))
     assert u == len(ref[0])
     assert_same(got, ref)
+
+
+def test_dedup_of_a_2p26_partition_output():
+    """The partition workload's PE output at 2^26 edges (2^15 buckets): the GPU's
+    duplicate removal against the oracle's first-occurrence filter of the
+    same array."""
+    k, t, m, seed = 26, 5, 1 << 26, 1
+    table = rm.rmat_build_table(*G500, k, 4096)
+    p = rm.rmat_partition_create(table, t, m, seed)
+    _, edges = rm.rmat_partition_info(p)
+    out = rm.empty_edges(edges, k)
+    rm.rmat_generate_partition(p, out)
+    torch.cuda.synchronize()
+    ref = oracle.dedup_first(*pairs(out, k))
+    u, got = _dedup_gpu(out, edges, k)
+    assert u == len(ref[0])
+    assert_same(got, ref)
+    del out
+    torch.cuda.empty_cache()
 
 
 def test_dedup_edge_cases():
@@ -152,6 +172,75 @@ def test_dedup_edge_cases():
     assert rm.rmat_dedup_edges(same, 0, 10) == 0
     with pytest.raises(rm.RmatError):
         rm.rmat_dedup_edges(same, 10, 32)
+
+
+def _to_device(h, out):
+    out.copy_(torch.from_numpy(np.ascontiguousarray(h).view(np.int32)))
+
+
+def test_dedup_heavy_repeats_use_the_overflow_table():
+    """Keys repeated more often than a shared-memory bucket holds (30000,
+    9000 and 7000 copies among 400000 edges) go through the device-memory
+    table; the result still equals the oracle's first-occurrence filter."""
+    k, m = 20, 400_000
+    t = rm.rmat_build_table(*G500, k, 256)
+    out = rm.empty_edges(m, k)
+    rm.rmat_generate(t, 5, 0, m, out)
+    torch.cuda.synchronize()
+    h = out.cpu().numpy().view(np.uint32).copy()
+    rng = np.random.default_rng(11)
+    for (r, c), copies in (((3, 5), 30_000), ((100, 7), 9_000), ((1, 1), 7_000)):
+        at = rng.choice(m, copies, replace=False)
+        h[at, 0], h[at, 1] = r, c
+    _to_device(h, out)
+    ref = oracle.dedup_first(h[:, 0].astype(np.uint64), h[:, 1].astype(np.uint64))
+    u, got = _dedup_gpu(out, m, k)
+    assert u == len(ref[0])
+    assert_same(got, ref)
+
+
+def test_dedup_of_two_keys_in_4m_edges():
+    """2^22 edges alternating between two keys: at most two buckets, each of
+    about 2^21 edges, both far above the shared-memory limit."""
+    k, m = 16, 1 << 22
+    h = np.empty((m, 2), np.uint32)
+    h[0::2] = (9, 4)
+    h[1::2] = (4, 9)
+    out = rm.empty_edges(m, k)
+    _to_device(h, out)
+    u, got = _dedup_gpu(out, m, k)
+    assert u == 2
+    assert got[0].tolist() == [9, 4] and got[1].tolist() == [4, 9]
+
+
+def test_dedup_of_distinct_edges_keeps_all():
+    """(2^21 + 5) distinct edges in a scrambled order (two levels of buckets,
+    a ragged bitmap tail): nothing is removed and the order is kept."""
+    k, m = 22, (1 << 21) + 5
+    rng = np.random.default_rng(2)
+    v = rng.permutation(1 << 22)[:m].astype(np.uint32)
+    h = np.stack([v, (v * 7 + 3) & ((1 << 22) - 1)], axis=1).astype(np.uint32)
+    out = rm.empty_edges(m, k)
+    _to_device(h, out)
+    u, got = _dedup_gpu(out, m, k)
+    assert u == m
+    assert np.array_equal(got[0], h[:, 0]) and np.array_equal(got[1], h[:, 1])
+
+
+def test_dedup_release_and_reuse():
+    """The kept scratch is freed on request; the next call allocates it again
+    and gives the same result; releasing twice is harmless."""
+    k, m = 14, 123_457
+    t = rm.rmat_build_table(*G500, k, 256)
+    out = rm.empty_edges(m, k)
+    rm.rmat_generate(t, 8, 0, m, out)
+    keep = out.clone()
+    u1, got1 = _dedup_gpu(out, m, k)
+    rm.rmat_dedup_release()
+    rm.rmat_dedup_release()
+    u2, got2 = _dedup_gpu(keep, m, k)
+    assert u1 == u2
+    assert_same(got2, got1)
 
 
 def test_partitioned_dedup_is_local():

@@ -36,6 +36,7 @@
 #include <string>
 #include <vector>
 
+#include "rmat_device.cuh"
 #include "rmat_internal.h"
 #include "rmat_kernels.h"
 
@@ -53,7 +54,8 @@ constexpr uint64_t kLocalTarget = 2048;            // mean edges per bucket, at 
 constexpr uint32_t kLocalMax = 6144;               // largest bucket done in shared memory
 constexpr uint32_t kLocalSlots = 8192;             // its table: load <= 0.75
 constexpr int kLocalThreads = 512;
-constexpr size_t kLocalSmem = size_t(kLocalSlots) * 12;  // keys and smallest indices
+constexpr int kLocalCtas = 2;                      // per SM (112 KB of shared memory each)
+constexpr size_t kLocalSmem = size_t(kLocalMax) * 8 + size_t(kLocalSlots) * 8;  // hashes; owners, smallest indices
 static_assert((1 << kL2MaxBits) == kBlock, "one sub-bucket counter per thread of the split");
 
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
@@ -120,34 +122,83 @@ __global__ void __launch_bounds__(kBlock) k_dd_hist(const uint2 *edges, uint64_t
 // and written out so that consecutive threads write consecutive entries of a
 // run (a run is written in one burst, so L2 merges the partial lines at its
 // ends with the neighbouring runs instead of evicting them half written).
+// When `edges` is 16-byte aligned, the next tile is fetched into shared
+// memory by a bulk copy while this one is ranked, staged and written (an
+// odd last edge of a tile is read directly).
 constexpr int kScatterTile = 8192;
 constexpr int kScatterPer = kScatterTile / kBlock;
-constexpr size_t kScatterSmem = size_t(kScatterTile) * (8 + 4 + 2) + 3 * 4 * (size_t(1) << kL1MaxBits);
+constexpr size_t kScatterIn = 16;                                   // after the mbarrier
+constexpr size_t kScatterKey = kScatterIn + size_t(kScatterTile) * 8;
+constexpr size_t kScatterPos = kScatterKey + size_t(kScatterTile) * 8;
+constexpr size_t kScatterDig = kScatterPos + size_t(kScatterTile) * 2;
+constexpr size_t kScatterCnt = kScatterDig + size_t(kScatterTile) * 2;
+constexpr size_t kScatterSmem = kScatterCnt + 3 * 4 * (size_t(1) << kL1MaxBits);
+constexpr uint32_t kWaitLimit = 1u << 22;                           // polls of a bounded mbarrier wait
 static_assert((1 << kL1MaxBits) <= kBlock, "one bucket counter per thread of the scatter");
 __global__ void __launch_bounds__(kBlock, 1) k_dd_scatter(const uint2 *edges, uint64_t n, int k, int bits,
-                                                          uint32_t *cursor, uint64_t *bhash, uint32_t *bidx) {
+                                                          uint32_t *cursor, uint64_t *bhash, uint32_t *bidx,
+                                                          unsigned *err) {
     extern __shared__ __align__(16) unsigned char dsm[];
-    auto *skey = reinterpret_cast<uint64_t *>(dsm);
-    auto *sidx = reinterpret_cast<uint32_t *>(dsm + size_t(kScatterTile) * 8);
-    auto *sdig = reinterpret_cast<uint16_t *>(dsm + size_t(kScatterTile) * 12);
-    auto *cnt = reinterpret_cast<uint32_t *>(dsm + size_t(kScatterTile) * 14);
+    auto *mbar = reinterpret_cast<uint64_t *>(dsm);
+    auto *in = reinterpret_cast<uint2 *>(dsm + kScatterIn);
+    auto *skey = reinterpret_cast<uint64_t *>(dsm + kScatterKey);
+    auto *spos = reinterpret_cast<uint16_t *>(dsm + kScatterPos);
+    auto *sdig = reinterpret_cast<uint16_t *>(dsm + kScatterDig);
+    auto *cnt = reinterpret_cast<uint32_t *>(dsm + kScatterCnt);
     uint32_t *off = cnt + (1u << kL1MaxBits);
     uint32_t *gbase = off + (1u << kL1MaxBits);
     __shared__ uint32_t ws[32];
     const uint32_t t = threadIdx.x;
     const uint64_t tiles = (n + kScatterTile - 1) / kScatterTile;
+    const bool tma = (reinterpret_cast<uintptr_t>(edges) & 15u) == 0;
+    // edges of tile `tile` that the bulk copy brings (an even number)
+    auto copied = [&](uint64_t tile) -> uint32_t {
+        if (!tma || tile >= tiles) return 0u;
+        const uint64_t t0 = tile * kScatterTile;
+        return uint32_t(min(uint64_t(kScatterTile), n - t0)) & ~1u;
+    };
+    auto issue = [&](uint64_t tile) {  // thread 0
+        const uint32_t c = copied(tile);
+        if (!c) return;
+        dev::fence_proxy_async_smem();
+        dev::mbar_arrive_expect_tx(mbar, c * 8u);
+        const unsigned char *src = reinterpret_cast<const unsigned char *>(edges + tile * kScatterTile);
+        for (uint32_t o = 0; o < c * 8u; o += 32768u)
+            dev::bulk_g2s(reinterpret_cast<unsigned char *>(in) + o, src + o, min(32768u, c * 8u - o), mbar);
+    };
+    if (t == 0) {
+        dev::mbar_init(mbar, 1);
+        dev::fence_mbar_init();
+    }
     cnt[t] = 0;
     __syncthreads();
+    if (t == 0) issue(blockIdx.x);
+    uint32_t parity = 0;
     for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const uint64_t t0 = tile * kScatterTile;
         const uint32_t tn = uint32_t(min(uint64_t(kScatterTile), n - t0));
+        const uint32_t nc = copied(tile);
+        if (nc) {
+            const bool ok = __syncthreads_and(dev::mbar_wait_bounded(mbar, parity, kWaitLimit)) != 0;
+            parity ^= 1u;
+            if (!ok) {  // never expected: give the copy one more bounded wait, then stop
+                if (t == 0) atomicOr(err, 16u);
+                dev::mbar_wait_bounded(mbar, parity ^ 1u, kWaitLimit);
+                return;
+            }
+        }
         uint64_t h[kScatterPer];
         uint32_t dig[kScatterPer], rank[kScatterPer];
 #pragma unroll
         for (int u = 0; u < kScatterPer; ++u) {
             const uint32_t i = u * kBlock + t;
-            h[u] = i < tn ? edge_key(edges, t0 + i, k) : 0;
+            uint2 v = make_uint2(0, 0);
+            if (i < nc) v = in[i];
+            else if (i < tn) v = edges[t0 + i];
+            h[u] = (uint64_t(v.x) << k) | v.y;
         }
+        __syncthreads();  // the copy buffer is free
+        if (t == 0) issue(tile + gridDim.x);
 #pragma unroll
         for (int u = 0; u < kScatterPer; ++u) {
             h[u] = mix64(h[u]);
@@ -166,7 +217,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_dd_scatter(const uint2 *edges, ui
             if (i >= tn) continue;
             const uint32_t p = off[dig[u]] + rank[u];
             skey[p] = h[u];
-            sidx[p] = uint32_t(t0 + i);
+            spos[p] = uint16_t(i);
             sdig[p] = uint16_t(dig[u]);
         }
         gbase[t] = gb;
@@ -178,7 +229,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_dd_scatter(const uint2 *edges, ui
             const uint32_t d = sdig[p];
             const uint32_t g = gbase[d] + (p - off[d]);
             bhash[g] = skey[p];
-            bidx[g] = sidx[p];
+            bidx[g] = uint32_t(t0) + spos[p];
         }
         cnt[t] = 0;
         __syncthreads();
@@ -191,18 +242,29 @@ __global__ void __launch_bounds__(kBlock, 1) k_dd_scatter(const uint2 *edges, ui
 // sub-bucket in sub_start[b * 2^B2 + d]; then the bucket a tile of
 // kSplitTile entries at a time, staged in shared memory sorted by sub-bucket
 // as in the level-1 scatter, into (bkey, bidx).  The block owns its bucket, so
-// the sub-bucket cursors live in shared memory.
+// the sub-bucket cursors live in shared memory.  The next tile comes into
+// shared memory by two bulk copies (hashes and indices, widened to 16-byte
+// boundaries) while this one is ranked, staged and written.
 constexpr int kSplitTile = 4096;
 constexpr int kSplitPer = kSplitTile / kBlock;
-constexpr size_t kSplitSmem = size_t(kSplitTile) * (8 + 4 + 2) + 4 * 4 * (size_t(1) << kL2MaxBits);
+constexpr size_t kSplitInH = 16;                                     // after the mbarrier
+constexpr size_t kSplitInI = kSplitInH + size_t(kSplitTile + 8) * 8;
+constexpr size_t kSplitKey = kSplitInI + size_t(kSplitTile + 8) * 4;
+constexpr size_t kSplitIdx = kSplitKey + size_t(kSplitTile) * 8;
+constexpr size_t kSplitDig = kSplitIdx + size_t(kSplitTile) * 4;
+constexpr size_t kSplitCnt = kSplitDig + size_t(kSplitTile) * 2;
+constexpr size_t kSplitSmem = kSplitCnt + 4 * 4 * (size_t(1) << kL2MaxBits);
 __global__ void __launch_bounds__(kBlock, 1) k_dd_split(const uint64_t *akey, const uint32_t *aidx, const uint32_t *lo1,
                                                         const uint32_t *hi1, int B, int B2, uint64_t *bkey,
-                                                        uint32_t *bidx, uint32_t *sub_start) {
+                                                        uint32_t *bidx, uint32_t *sub_start, unsigned *err) {
     extern __shared__ __align__(16) unsigned char dsm[];
-    auto *skey = reinterpret_cast<uint64_t *>(dsm);
-    auto *sidx = reinterpret_cast<uint32_t *>(dsm + size_t(kSplitTile) * 8);
-    auto *sdig = reinterpret_cast<uint16_t *>(dsm + size_t(kSplitTile) * 12);
-    auto *cnt = reinterpret_cast<uint32_t *>(dsm + size_t(kSplitTile) * 14);
+    auto *mbar = reinterpret_cast<uint64_t *>(dsm);
+    auto *inh = reinterpret_cast<uint64_t *>(dsm + kSplitInH);
+    auto *ini = reinterpret_cast<uint32_t *>(dsm + kSplitInI);
+    auto *skey = reinterpret_cast<uint64_t *>(dsm + kSplitKey);
+    auto *sidx = reinterpret_cast<uint32_t *>(dsm + kSplitIdx);
+    auto *sdig = reinterpret_cast<uint16_t *>(dsm + kSplitDig);
+    auto *cnt = reinterpret_cast<uint32_t *>(dsm + kSplitCnt);
     uint32_t *off = cnt + (1u << kL2MaxBits);
     uint32_t *base = off + (1u << kL2MaxBits);
     uint32_t *cur = base + (1u << kL2MaxBits);
@@ -212,17 +274,21 @@ __global__ void __launch_bounds__(kBlock, 1) k_dd_split(const uint64_t *akey, co
     const uint32_t nd = 1u << B2, dmask = nd - 1;
     const int sh = 64 - B;
     auto digit = [&](uint64_t h) { return uint32_t(h >> sh) & dmask; };
+    if (t == 0) {
+        dev::mbar_init(mbar, 1);
+        dev::fence_mbar_init();
+    }
     cnt[t] = 0;
     __syncthreads();
-    for (uint32_t j0 = lo + t; j0 < hi; j0 += 4 * kBlock) {
-        uint64_t key[4];
+    for (uint32_t j0 = lo + t; j0 < hi; j0 += 8 * kBlock) {
+        uint64_t key[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 8; ++u) {
             const uint32_t j = j0 + u * kBlock;
             key[u] = j < hi ? akey[j] : 0;
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 8; ++u)
             if (j0 + u * kBlock < hi) atomicAdd(&cnt[digit(key[u])], 1u);
     }
     __syncthreads();
@@ -234,20 +300,41 @@ __global__ void __launch_bounds__(kBlock, 1) k_dd_split(const uint64_t *akey, co
         cnt[t] = 0;
     }
     __syncthreads();
-    uint64_t key[kSplitPer];
-    uint32_t idx[kSplitPer];
-    auto load = [&](uint32_t j0) {
-        const uint32_t tn = j0 < hi ? min(uint32_t(kSplitTile), hi - j0) : 0u;
+    // the tile at j0: hashes [j0 & ~1, even end), indices [j0 & ~3, end rounded
+    // up to 4), so that both copies start and end on 16-byte boundaries (the
+    // widening reads at most three entries past the bucket, still inside the
+    // scratch)
+    auto issue = [&](uint32_t j0) {  // thread 0
+        const uint32_t tn = min(uint32_t(kSplitTile), hi - j0);
+        const uint32_t ah = j0 & ~1u, eh = (j0 + tn + 1) & ~1u;
+        const uint32_t ai = j0 & ~3u, ei = (j0 + tn + 3) & ~3u;
+        dev::fence_proxy_async_smem();
+        dev::mbar_arrive_expect_tx(mbar, (eh - ah) * 8u + (ei - ai) * 4u);
+        dev::bulk_g2s(inh, akey + ah, (eh - ah) * 8u, mbar);
+        dev::bulk_g2s(ini, aidx + ai, (ei - ai) * 4u, mbar);
+    };
+    if (t == 0 && lo < hi) issue(lo);
+    uint32_t parity = 0;
+    for (uint32_t j0 = lo; j0 < hi; j0 += kSplitTile) {
+        const uint32_t tn = min(uint32_t(kSplitTile), hi - j0);
+        const bool ok = __syncthreads_and(dev::mbar_wait_bounded(mbar, parity, kWaitLimit)) != 0;
+        parity ^= 1u;
+        if (!ok) {  // never expected: give the copy one more bounded wait, then stop
+            if (t == 0) atomicOr(err, 32u);
+            dev::mbar_wait_bounded(mbar, parity ^ 1u, kWaitLimit);
+            return;
+        }
+        uint64_t key[kSplitPer];
+        uint32_t idx[kSplitPer];
+        const uint32_t dh = j0 & 1u, di = j0 & 3u;
 #pragma unroll
         for (int u = 0; u < kSplitPer; ++u) {
             const uint32_t i = u * kBlock + t;
-            key[u] = i < tn ? akey[j0 + i] : 0;
-            idx[u] = i < tn ? aidx[j0 + i] : 0;
+            key[u] = i < tn ? inh[dh + i] : 0;
+            idx[u] = i < tn ? ini[di + i] : 0;
         }
-    };
-    load(lo);
-    for (uint32_t j0 = lo; j0 < hi; j0 += kSplitTile) {
-        const uint32_t tn = min(uint32_t(kSplitTile), hi - j0);
+        __syncthreads();  // the copy buffers are free
+        if (t == 0 && j0 + kSplitTile < hi) issue(j0 + kSplitTile);
         uint32_t dig[kSplitPer], rank[kSplitPer];
 #pragma unroll
         for (int u = 0; u < kSplitPer; ++u) {
@@ -268,7 +355,6 @@ __global__ void __launch_bounds__(kBlock, 1) k_dd_split(const uint64_t *akey, co
             sidx[p] = idx[u];
             sdig[p] = uint16_t(dig[u]);
         }
-        load(j0 + kSplitTile);
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < kSplitPer; ++u) {
@@ -285,26 +371,27 @@ __global__ void __launch_bounds__(kBlock, 1) k_dd_split(const uint64_t *akey, co
 }
 
 // 4. Bucket s = blockIdx.x, entries [starts[s], starts[s + 1]) (n for the
-// last), deduplicated in shared memory.  The table has T slots, a power of two
-// at least twice the bucket (at most kLocalSlots, so a bucket of at most
-// kLocalMax edges always finds a free slot within T probes).  A key's slot
-// never changes once claimed, and every copy of the key probes the same
-// sequence, so all copies meet in one slot; each lowers the slot's index to
-// its own, and after the barrier every copy that does not hold the minimum
-// clears its survivor bit.  The table holds hashes (equal hashes, equal
-// edges); an empty slot holds a value whose top B bits are not s, so no hash
-// of this bucket.  A thread keeps its edges' indices and slots in registers
-// (at most kLocalBatches x 4 edges), and the first edges' loads are in flight
-// while the table is cleared.  A larger bucket goes to the overflow list
-// (ovf[0] = how many, ovf[1 + i] = bucket).
+// last), deduplicated in shared memory.  The bucket's hashes are staged in
+// shared memory (entry r at sh[r]; equal hashes, equal edges), and a table of
+// T slots, a power of two at least twice the bucket (at most kLocalSlots, so a
+// bucket of at most kLocalMax edges always finds a free slot within T probes),
+// holds in own[slot] 1 + the entry that claimed it (0 = free; claimed by a
+// 32-bit CAS) and in low[slot] the smallest edge index of that entry's key.
+// A slot's owner never changes once set, and every copy of a key probes the
+// same sequence, so all copies meet in one slot; each lowers low[] to its own
+// index, and after the barrier every copy that does not hold the minimum
+// clears its survivor bit.  A thread keeps its edges' indices and slots in
+// registers (at most kLocalBatches x 4 edges).  A larger bucket goes to the
+// overflow list (ovf[0] = how many, ovf[1 + i] = bucket).
 constexpr int kLocalBatches = int(kLocalMax / (4 * kLocalThreads));
 static_assert(kLocalBatches * 4 * kLocalThreads == int(kLocalMax), "whole batches of four edges per thread");
-__global__ void __launch_bounds__(kLocalThreads, 2) k_dd_local(const uint64_t *hash, const uint32_t *idx,
-                                                               const uint32_t *starts, uint32_t nsub, int B, uint32_t n,
+__global__ void __launch_bounds__(kLocalThreads, kLocalCtas) k_dd_local(const uint64_t *hash, const uint32_t *idx,
+                                                               const uint32_t *starts, uint32_t nsub, uint32_t n,
                                                                uint32_t *bitmap, uint32_t *ovf, unsigned *err) {
     extern __shared__ __align__(16) unsigned char dsm[];
-    auto *skey = reinterpret_cast<unsigned long long *>(dsm);
-    auto *sidx = reinterpret_cast<uint32_t *>(dsm + size_t(kLocalSlots) * 8);
+    auto *sh = reinterpret_cast<uint64_t *>(dsm);
+    auto *own = reinterpret_cast<uint32_t *>(dsm + size_t(kLocalMax) * 8);
+    auto *low = own + kLocalSlots;
     const uint32_t s = blockIdx.x;
     const uint32_t lo = starts[s], hi = s + 1 < nsub ? starts[s + 1] : n;
     const uint32_t cnt = hi - lo;
@@ -317,44 +404,46 @@ __global__ void __launch_bounds__(kLocalThreads, 2) k_dd_local(const uint64_t *h
     while (T < 2 * cnt && T < kLocalSlots) T <<= 1;
     const uint32_t tmask = T - 1;
     const int batches = int((cnt + 4 * kLocalThreads - 1) / (4 * kLocalThreads));
-    const unsigned long long empty = uint64_t(s ^ 1u) << (64 - B);  // B >= 1
-    uint64_t kk[4];
     uint32_t id[4 * kLocalBatches], sl[4 * kLocalBatches];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const uint32_t r = threadIdx.x + u * kLocalThreads;
-        kk[u] = r < cnt ? hash[lo + r] : 0;
-        id[u] = r < cnt ? idx[lo + r] : 0;
+    for (int bt = 0; bt < kLocalBatches; ++bt) {
+        if (bt >= batches) break;
+        uint64_t hv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t r = threadIdx.x + (bt * 4 + u) * kLocalThreads;
+            hv[u] = r < cnt ? hash[lo + r] : 0;
+            id[bt * 4 + u] = r < cnt ? idx[lo + r] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t r = threadIdx.x + (bt * 4 + u) * kLocalThreads;
+            if (r < cnt) sh[r] = hv[u];
+        }
     }
     for (uint32_t i = threadIdx.x; i < T; i += kLocalThreads) {
-        skey[i] = empty;
-        sidx[i] = ~0u;
+        own[i] = 0;
+        low[i] = ~0u;
     }
     __syncthreads();
-    volatile unsigned long long *vkey = skey;
+    volatile uint32_t *vown = own;
     bool lost = false;
 #pragma unroll
     for (int bt = 0; bt < kLocalBatches; ++bt) {
         if (bt >= batches) break;
-        if (bt > 0) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const uint32_t r = threadIdx.x + (bt * 4 + u) * kLocalThreads;
-                kk[u] = r < cnt ? hash[lo + r] : 0;
-                id[bt * 4 + u] = r < cnt ? idx[lo + r] : 0;
-            }
-        }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int e = bt * 4 + u;
+            const uint32_t r = threadIdx.x + e * kLocalThreads;
             sl[e] = 0;
-            if (threadIdx.x + e * kLocalThreads >= cnt) continue;
-            uint32_t h = uint32_t(kk[u]) & tmask;
+            if (r >= cnt) continue;
+            const uint64_t hv = sh[r];
+            uint32_t h = uint32_t(hv) & tmask;
             bool placed = false;
             for (uint32_t probe = 0; probe < T; ++probe) {
-                unsigned long long c = vkey[h];
-                if (c == empty) c = atomicCAS(&skey[h], empty, (unsigned long long)kk[u]);
-                if (c == empty || c == kk[u]) {
+                uint32_t o = vown[h];
+                if (o == 0) o = atomicCAS(&own[h], 0u, r + 1);
+                if (o == 0 || sh[o - 1] == hv) {
                     placed = true;
                     break;
                 }
@@ -364,7 +453,7 @@ __global__ void __launch_bounds__(kLocalThreads, 2) k_dd_local(const uint64_t *h
                 lost = true;
                 h = 0;
             }
-            atomicMin(&sidx[h], id[e]);
+            atomicMin(&low[h], id[e]);
             sl[e] = h;
         }
     }
@@ -377,7 +466,7 @@ __global__ void __launch_bounds__(kLocalThreads, 2) k_dd_local(const uint64_t *h
         for (int u = 0; u < 4; ++u) {
             const int e = bt * 4 + u;
             if (threadIdx.x + e * kLocalThreads >= cnt) continue;
-            if (sidx[sl[e]] != id[e]) atomicAnd(bitmap + (id[e] >> 5), ~(1u << (id[e] & 31)));
+            if (low[sl[e]] != id[e]) atomicAnd(bitmap + (id[e] >> 5), ~(1u << (id[e] & 31)));
         }
     }
 }
@@ -588,7 +677,7 @@ extern "C" rmat_status rmat_dedup_edges(void *edges, uint64_t count, int k, uint
     };
 
     // B bits of buckets (mean size at most kLocalTarget), B1 of them at level 1
-    int B = 1;  // at least two buckets: an empty local slot is marked by the other bucket's number
+    int B = 0;
     while (B < kMaxBits && (count >> B) > kLocalTarget) ++B;
     const int B1 = std::min(B, kL1MaxBits), B2 = B - B1;
     const uint32_t nb1 = 1u << B1, nsub = 1u << B;
@@ -603,10 +692,10 @@ extern "C" rmat_status rmat_dedup_edges(void *edges, uint64_t count, int k, uint
     const size_t off_sub = off_cursor + up(4 * size_t(nb1));
     const size_t off_ovf = off_sub + up(4 * size_t(nsub));
     const size_t off_akey = off_ovf + up(4 * (size_t(nsub) + 1));
-    const size_t off_bkey = off_akey + up(8 * count);
-    const size_t off_aidx = off_bkey + up(8 * count);
-    const size_t off_bidx = off_aidx + up(4 * count);
-    const size_t off_bits = off_bidx + up(4 * count);
+    const size_t off_bkey = off_akey + up(8 * count + 256);  // 256 bytes of slack after each array: the
+    const size_t off_aidx = off_bkey + up(8 * count + 256);  // split's widened copies read a few entries
+    const size_t off_bidx = off_aidx + up(4 * count + 256);  // past a bucket
+    const size_t off_bits = off_bidx + up(4 * count + 256);
     const size_t off_cnt = off_bits + up(4 * words);
     const size_t off_tot = off_cnt + up(4 * chunks);
     const size_t bytes = off_tot + 256;
@@ -661,7 +750,7 @@ extern "C" rmat_status rmat_dedup_edges(void *edges, uint64_t count, int k, uint
     if (e == cudaSuccess) {
         const uint64_t tiles = (count + kScatterTile - 1) / kScatterTile;
         const unsigned sgrid = unsigned(std::min<uint64_t>(tiles, uint64_t(props.sms)));
-        k_dd_scatter<<<sgrid, kBlock, kScatterSmem, stream>>>(src, count, k, B1, cursor, akey, aidx);
+        k_dd_scatter<<<sgrid, kBlock, kScatterSmem, stream>>>(src, count, k, B1, cursor, akey, aidx, err);
         e = cudaGetLastError();
     }
     // 3. level-2 split (cursor[b] now ends level-1 bucket b)
@@ -671,7 +760,7 @@ extern "C" rmat_status rmat_dedup_edges(void *edges, uint64_t count, int k, uint
     if (e == cudaSuccess && B2 > 0)
         e = cudaFuncSetAttribute(k_dd_split, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSplitSmem));
     if (e == cudaSuccess && B2 > 0) {
-        k_dd_split<<<nb1, kBlock, kSplitSmem, stream>>>(akey, aidx, start1, cursor, B, B2, bkey, bidx, sub);
+        k_dd_split<<<nb1, kBlock, kSplitSmem, stream>>>(akey, aidx, start1, cursor, B, B2, bkey, bidx, sub, err);
         e = cudaGetLastError();
         lkey = bkey;
         lidx = bidx;
@@ -682,7 +771,7 @@ extern "C" rmat_status rmat_dedup_edges(void *edges, uint64_t count, int k, uint
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_dd_local, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kLocalSmem));
     if (e == cudaSuccess) {
-        k_dd_local<<<nsub, kLocalThreads, kLocalSmem, stream>>>(lkey, lidx, starts, nsub, B, n, bitmap, ovf, err);
+        k_dd_local<<<nsub, kLocalThreads, kLocalSmem, stream>>>(lkey, lidx, starts, nsub, n, bitmap, ovf, err);
         e = cudaGetLastError();
     }
     uint32_t novf = 0;

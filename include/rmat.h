@@ -353,7 +353,7 @@ void rmat_free_partition(rmat_partition *p);
  * `stream`; count <= 2^31.  Device scratch of about 24 bytes per edge is
  * allocated by the first call on a device and kept for later calls there
  * (grown when a call needs more; rmat_dedup_release frees it); calls on one
- * device take turns on it under a lock.  A hash bucket of more than 6144
+ * device take turns on it under a lock.  A hash bucket of more than 3072
  * edges (possible only when few keys repeat many times) is done in a device
  * table of 16-byte slots, a power of two at least twice that bucket, that the
  * call allocates and frees.  Errors: RMAT_ERR_INVALID_ARGUMENT (k, count,

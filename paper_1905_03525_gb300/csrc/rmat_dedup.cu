@@ -51,12 +51,12 @@ constexpr int kL1MaxBits = 10;                     // level-1 buckets: at most 1
 constexpr int kMaxBits = 20;                       // buckets in all: at most 2^20
 constexpr int kL2MaxBits = kMaxBits - kL1MaxBits;  // sub-buckets per level-1 bucket: at most 1024
 constexpr uint64_t kLocalTarget = 2048;            // mean edges per bucket, at most
-constexpr uint32_t kLocalMax = 6144;               // largest bucket done in shared memory
-constexpr uint32_t kLocalSlots = 8192;             // its table: load <= 0.75
+constexpr uint32_t kLocalMax = 3072;               // largest bucket done in shared memory
+constexpr uint32_t kLocalSlots = 4096;             // its table: load <= 0.75
 constexpr int kLocalThreads = 512;
-constexpr int kLocalCtas = 2;                      // per SM (112 KB of shared memory each)
+constexpr int kLocalCtas = 4;                      // per SM (56 KB of shared memory each)
+constexpr int kLocalPer = 2;                       // edges per thread and batch
 constexpr size_t kLocalSmem = size_t(kLocalMax) * 8 + size_t(kLocalSlots) * 8;  // hashes; owners, smallest indices
-static_assert((1 << kL2MaxBits) == kBlock, "one sub-bucket counter per thread of the split");
 
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
     // splitmix64 finaliser (Steele, Lea, Flood 2014) as the hash; a bijection
@@ -76,8 +76,10 @@ __device__ __forceinline__ uint64_t edge_key(const uint2 *e, uint64_t i, int k) 
 // The top `bits` bits of a hash (0 when bits = 0).
 __device__ __forceinline__ uint32_t top_bits(uint64_t h, int bits) { return bits ? uint32_t(h >> (64 - bits)) : 0u; }
 
-// Exclusive prefix sum over a block of kBlock threads, one value each; `ws`
-// holds 32 words.  Every thread of the block calls it.
+// Exclusive prefix sum over a block of NT threads (a multiple of 32, at most
+// 1024), one value each; `ws` holds 32 words.  Every thread of the block
+// calls it.
+template <int NT>
 __device__ __forceinline__ uint32_t block_exclusive(uint32_t v, uint32_t *ws) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t x = v;
@@ -89,7 +91,7 @@ __device__ __forceinline__ uint32_t block_exclusive(uint32_t v, uint32_t *ws) {
     if (lane == 31) ws[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        uint32_t y = ws[lane];
+        uint32_t y = lane < NT / 32 ? ws[lane] : 0u;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_dd_scatter(const uint2 *edges, ui
         }
         __syncthreads();
         const uint32_t c = cnt[t];  // 0 past the last bucket
-        const uint32_t ex = block_exclusive(c, ws);
+        const uint32_t ex = block_exclusive<kBlock>(c, ws);
         off[t] = ex;
         const uint32_t gb = c ? atomicAdd(&cursor[t], c) : 0u;  // used after the staging
         __syncthreads();
@@ -244,32 +246,36 @@ __global__ void __launch_bounds__(kBlock, 1) k_dd_scatter(const uint2 *edges, ui
 // as in the level-1 scatter, into (bkey, bidx).  The block owns its bucket, so
 // the sub-bucket cursors live in shared memory.  The next tile comes into
 // shared memory by two bulk copies (hashes and indices, widened to 16-byte
-// boundaries) while this one is ranked, staged and written.
-constexpr int kSplitTile = 4096;
-constexpr int kSplitPer = kSplitTile / kBlock;
+// boundaries) while this one is ranked, staged and written.  One block per
+// SM; each thread owns kSplitDpt sub-bucket counters.
+constexpr int kSplitThreads = 1024;
+constexpr int kSplitTile = 8192;
+constexpr int kSplitPer = kSplitTile / kSplitThreads;
+constexpr uint32_t kSplitDigits = 1u << kL2MaxBits;
+constexpr int kSplitDpt = int(kSplitDigits) / kSplitThreads;
+static_assert(kSplitDpt * kSplitThreads == int(kSplitDigits), "whole sub-bucket counters per thread of the split");
 constexpr size_t kSplitInH = 16;                                     // after the mbarrier
 constexpr size_t kSplitInI = kSplitInH + size_t(kSplitTile + 8) * 8;
 constexpr size_t kSplitKey = kSplitInI + size_t(kSplitTile + 8) * 4;
 constexpr size_t kSplitIdx = kSplitKey + size_t(kSplitTile) * 8;
-constexpr size_t kSplitDig = kSplitIdx + size_t(kSplitTile) * 4;
-constexpr size_t kSplitCnt = kSplitDig + size_t(kSplitTile) * 2;
-constexpr size_t kSplitSmem = kSplitCnt + 4 * 4 * (size_t(1) << kL2MaxBits);
-__global__ void __launch_bounds__(kBlock, 1) k_dd_split(const uint64_t *akey, const uint32_t *aidx, const uint32_t *lo1,
-                                                        const uint32_t *hi1, int B, int B2, uint64_t *bkey,
-                                                        uint32_t *bidx, uint32_t *sub_start, unsigned *err) {
+constexpr size_t kSplitCnt = kSplitIdx + size_t(kSplitTile) * 4;
+constexpr size_t kSplitSmem = kSplitCnt + 4 * 4 * size_t(kSplitDigits);
+__global__ void __launch_bounds__(kSplitThreads, 1) k_dd_split(const uint64_t *akey, const uint32_t *aidx,
+                                                               const uint32_t *lo1, const uint32_t *hi1, int B,
+                                                               int B2, uint64_t *bkey, uint32_t *bidx,
+                                                               uint32_t *sub_start, unsigned *err) {
     extern __shared__ __align__(16) unsigned char dsm[];
     auto *mbar = reinterpret_cast<uint64_t *>(dsm);
     auto *inh = reinterpret_cast<uint64_t *>(dsm + kSplitInH);
     auto *ini = reinterpret_cast<uint32_t *>(dsm + kSplitInI);
     auto *skey = reinterpret_cast<uint64_t *>(dsm + kSplitKey);
     auto *sidx = reinterpret_cast<uint32_t *>(dsm + kSplitIdx);
-    auto *sdig = reinterpret_cast<uint16_t *>(dsm + kSplitDig);
     auto *cnt = reinterpret_cast<uint32_t *>(dsm + kSplitCnt);
-    uint32_t *off = cnt + (1u << kL2MaxBits);
-    uint32_t *base = off + (1u << kL2MaxBits);
-    uint32_t *cur = base + (1u << kL2MaxBits);
+    uint32_t *off = cnt + kSplitDigits;
+    uint32_t *base = off + kSplitDigits;
+    uint32_t *cur = base + kSplitDigits;
     __shared__ uint32_t ws[32];
-    const uint32_t t = threadIdx.x;
+    const uint32_t t = threadIdx.x, d0 = kSplitDpt * t;  // this thread's counters: d0 .. d0 + kSplitDpt - 1
     const uint32_t b = blockIdx.x, lo = lo1[b], hi = hi1[b];
     const uint32_t nd = 1u << B2, dmask = nd - 1;
     const int sh = 64 - B;
@@ -278,26 +284,33 @@ __global__ void __launch_bounds__(kBlock, 1) k_dd_split(const uint64_t *akey, co
         dev::mbar_init(mbar, 1);
         dev::fence_mbar_init();
     }
-    cnt[t] = 0;
+#pragma unroll
+    for (int q = 0; q < kSplitDpt; ++q) cnt[d0 + q] = 0;
     __syncthreads();
-    for (uint32_t j0 = lo + t; j0 < hi; j0 += 8 * kBlock) {
+    for (uint32_t j0 = lo + t; j0 < hi; j0 += 8 * kSplitThreads) {
         uint64_t key[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const uint32_t j = j0 + u * kBlock;
+            const uint32_t j = j0 + u * kSplitThreads;
             key[u] = j < hi ? akey[j] : 0;
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u)
-            if (j0 + u * kBlock < hi) atomicAdd(&cnt[digit(key[u])], 1u);
+            if (j0 + u * kSplitThreads < hi) atomicAdd(&cnt[digit(key[u])], 1u);
     }
     __syncthreads();
     {
-        const uint32_t v = t < nd ? cnt[t] : 0u;
-        const uint32_t ex = block_exclusive(v, ws);
-        if (t < nd) sub_start[(b << B2) + t] = lo + ex;
-        cur[t] = lo + ex;
-        cnt[t] = 0;
+        uint32_t v[kSplitDpt], sum = 0;  // 0 past the last sub-bucket
+#pragma unroll
+        for (int q = 0; q < kSplitDpt; ++q) sum += (v[q] = cnt[d0 + q]);
+        uint32_t e = lo + block_exclusive<kSplitThreads>(sum, ws);
+#pragma unroll
+        for (int q = 0; q < kSplitDpt; ++q) {
+            if (d0 + q < nd) sub_start[(b << B2) + d0 + q] = e;
+            cur[d0 + q] = e;
+            cnt[d0 + q] = 0;
+            e += v[q];
+        }
     }
     __syncthreads();
     // the tile at j0: hashes [j0 & ~1, even end), indices [j0 & ~3, end rounded
@@ -310,8 +323,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_dd_split(const uint64_t *akey, co
         const uint32_t ai = j0 & ~3u, ei = (j0 + tn + 3) & ~3u;
         dev::fence_proxy_async_smem();
         dev::mbar_arrive_expect_tx(mbar, (eh - ah) * 8u + (ei - ai) * 4u);
-        dev::bulk_g2s(inh, akey + ah, (eh - ah) * 8u, mbar);
-        dev::bulk_g2s(ini, aidx + ai, (ei - ai) * 4u, mbar);
+        auto copy = [&](void *dst, const void *src, uint32_t bytes) {  // pieces of at most 32 KB
+            for (uint32_t o = 0; o < bytes; o += 32768u)
+                dev::bulk_g2s(static_cast<unsigned char *>(dst) + o, static_cast<const unsigned char *>(src) + o,
+                              min(32768u, bytes - o), mbar);
+        };
+        copy(inh, akey + ah, (eh - ah) * 8u);
+        copy(ini, aidx + ai, (ei - ai) * 4u);
     };
     if (t == 0 && lo < hi) issue(lo);
     uint32_t parity = 0;
@@ -329,7 +347,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_dd_split(const uint64_t *akey, co
         const uint32_t dh = j0 & 1u, di = j0 & 3u;
 #pragma unroll
         for (int u = 0; u < kSplitPer; ++u) {
-            const uint32_t i = u * kBlock + t;
+            const uint32_t i = u * kSplitThreads + t;
             key[u] = i < tn ? inh[dh + i] : 0;
             idx[u] = i < tn ? ini[di + i] : 0;
         }
@@ -339,33 +357,42 @@ __global__ void __launch_bounds__(kBlock, 1) k_dd_split(const uint64_t *akey, co
 #pragma unroll
         for (int u = 0; u < kSplitPer; ++u) {
             dig[u] = digit(key[u]);
-            rank[u] = u * kBlock + t < tn ? atomicAdd(&cnt[dig[u]], 1u) : 0u;
+            rank[u] = u * kSplitThreads + t < tn ? atomicAdd(&cnt[dig[u]], 1u) : 0u;
         }
         __syncthreads();
-        const uint32_t c = cnt[t];  // 0 past the last sub-bucket
-        off[t] = block_exclusive(c, ws);
-        base[t] = cur[t];
-        cur[t] += c;
+        {
+            uint32_t c[kSplitDpt], sum = 0;
+#pragma unroll
+            for (int q = 0; q < kSplitDpt; ++q) sum += (c[q] = cnt[d0 + q]);
+            uint32_t o = block_exclusive<kSplitThreads>(sum, ws);
+#pragma unroll
+            for (int q = 0; q < kSplitDpt; ++q) {
+                off[d0 + q] = o;
+                base[d0 + q] = cur[d0 + q];
+                cur[d0 + q] += c[q];
+                o += c[q];
+            }
+        }
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < kSplitPer; ++u) {
-            if (u * kBlock + t >= tn) continue;
+            if (u * kSplitThreads + t >= tn) continue;
             const uint32_t p = off[dig[u]] + rank[u];
             skey[p] = key[u];
             sidx[p] = idx[u];
-            sdig[p] = uint16_t(dig[u]);
         }
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < kSplitPer; ++u) {
-            const uint32_t p = u * kBlock + t;
+            const uint32_t p = u * kSplitThreads + t;
             if (p >= tn) continue;
-            const uint32_t d = sdig[p];
-            const uint32_t g = base[d] + (p - off[d]);
-            bkey[g] = skey[p];
-            bidx[g] = sidx[p];
+            const uint64_t hv = skey[p];
+            const uint32_t d = digit(hv);
+            bkey[base[d] + (p - off[d])] = hv;
+            bidx[base[d] + (p - off[d])] = sidx[p];
         }
-        cnt[t] = 0;
+#pragma unroll
+        for (int q = 0; q < kSplitDpt; ++q) cnt[d0 + q] = 0;
         __syncthreads();
     }
 }
@@ -381,10 +408,10 @@ __global__ void __launch_bounds__(kBlock, 1) k_dd_split(const uint64_t *akey, co
 // same sequence, so all copies meet in one slot; each lowers low[] to its own
 // index, and after the barrier every copy that does not hold the minimum
 // clears its survivor bit.  A thread keeps its edges' indices and slots in
-// registers (at most kLocalBatches x 4 edges).  A larger bucket goes to the
-// overflow list (ovf[0] = how many, ovf[1 + i] = bucket).
-constexpr int kLocalBatches = int(kLocalMax / (4 * kLocalThreads));
-static_assert(kLocalBatches * 4 * kLocalThreads == int(kLocalMax), "whole batches of four edges per thread");
+// registers (at most kLocalBatches x kLocalPer edges).  A larger bucket goes
+// to the overflow list (ovf[0] = how many, ovf[1 + i] = bucket).
+constexpr int kLocalBatches = int(kLocalMax / (kLocalPer * kLocalThreads));
+static_assert(kLocalBatches * kLocalPer * kLocalThreads == int(kLocalMax), "whole batches per thread");
 __global__ void __launch_bounds__(kLocalThreads, kLocalCtas) k_dd_local(const uint64_t *hash, const uint32_t *idx,
                                                                const uint32_t *starts, uint32_t nsub, uint32_t n,
                                                                uint32_t *bitmap, uint32_t *ovf, unsigned *err) {
@@ -403,21 +430,21 @@ __global__ void __launch_bounds__(kLocalThreads, kLocalCtas) k_dd_local(const ui
     uint32_t T = 64;
     while (T < 2 * cnt && T < kLocalSlots) T <<= 1;
     const uint32_t tmask = T - 1;
-    const int batches = int((cnt + 4 * kLocalThreads - 1) / (4 * kLocalThreads));
-    uint32_t id[4 * kLocalBatches], sl[4 * kLocalBatches];
+    const int batches = int((cnt + kLocalPer * kLocalThreads - 1) / (kLocalPer * kLocalThreads));
+    uint32_t id[kLocalPer * kLocalBatches], sl[kLocalPer * kLocalBatches];
 #pragma unroll
     for (int bt = 0; bt < kLocalBatches; ++bt) {
         if (bt >= batches) break;
-        uint64_t hv[4];
+        uint64_t hv[kLocalPer];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const uint32_t r = threadIdx.x + (bt * 4 + u) * kLocalThreads;
+        for (int u = 0; u < kLocalPer; ++u) {
+            const uint32_t r = threadIdx.x + (bt * kLocalPer + u) * kLocalThreads;
             hv[u] = r < cnt ? hash[lo + r] : 0;
-            id[bt * 4 + u] = r < cnt ? idx[lo + r] : 0;
+            id[bt * kLocalPer + u] = r < cnt ? idx[lo + r] : 0;
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const uint32_t r = threadIdx.x + (bt * 4 + u) * kLocalThreads;
+        for (int u = 0; u < kLocalPer; ++u) {
+            const uint32_t r = threadIdx.x + (bt * kLocalPer + u) * kLocalThreads;
             if (r < cnt) sh[r] = hv[u];
         }
     }
@@ -432,8 +459,8 @@ __global__ void __launch_bounds__(kLocalThreads, kLocalCtas) k_dd_local(const ui
     for (int bt = 0; bt < kLocalBatches; ++bt) {
         if (bt >= batches) break;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int e = bt * 4 + u;
+        for (int u = 0; u < kLocalPer; ++u) {
+            const int e = bt * kLocalPer + u;
             const uint32_t r = threadIdx.x + e * kLocalThreads;
             sl[e] = 0;
             if (r >= cnt) continue;
@@ -463,8 +490,8 @@ __global__ void __launch_bounds__(kLocalThreads, kLocalCtas) k_dd_local(const ui
     for (int bt = 0; bt < kLocalBatches; ++bt) {
         if (bt >= batches) break;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int e = bt * 4 + u;
+        for (int u = 0; u < kLocalPer; ++u) {
+            const int e = bt * kLocalPer + u;
             if (threadIdx.x + e * kLocalThreads >= cnt) continue;
             if (low[sl[e]] != id[e]) atomicAnd(bitmap + (id[e] >> 5), ~(1u << (id[e] & 31)));
         }
@@ -633,7 +660,7 @@ __global__ void __launch_bounds__(kBlock) k_dd_compact(const uint2 *edges, uint6
         if (n - base < 4) keep &= (1u << (n - base)) - 1u;
     }
     const uint32_t c = __popc(keep);
-    uint64_t out = uint64_t(offsets[blockIdx.x]) + block_exclusive(c, ws);
+    uint64_t out = uint64_t(offsets[blockIdx.x]) + block_exclusive<kBlock>(c, ws);
 #pragma unroll
     for (int j = 0; j < kPerThread; ++j)
         if (keep & (1u << j)) dst[out++] = edges[base + j];
@@ -760,7 +787,7 @@ extern "C" rmat_status rmat_dedup_edges(void *edges, uint64_t count, int k, uint
     if (e == cudaSuccess && B2 > 0)
         e = cudaFuncSetAttribute(k_dd_split, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSplitSmem));
     if (e == cudaSuccess && B2 > 0) {
-        k_dd_split<<<nb1, kBlock, kSplitSmem, stream>>>(akey, aidx, start1, cursor, B, B2, bkey, bidx, sub, err);
+        k_dd_split<<<nb1, kSplitThreads, kSplitSmem, stream>>>(akey, aidx, start1, cursor, B, B2, bkey, bidx, sub, err);
         e = cudaGetLastError();
         lkey = bkey;
         lidx = bidx;

@@ -18,8 +18,9 @@
 //      counts the next B2 bits of h, scans them and scatters its edges into
 //      its sub-buckets (a second buffer, staged the same way), for
 //      2^(B1+B2) buckets of at most ~2048 edges on average;
-//   4. one CTA per bucket: an open-addressing table in shared memory (64-bit
-//      CAS claims a slot for a key, 32-bit atomicMin keeps the smallest edge
+//   4. one CTA per bucket: the bucket's hashes staged in shared memory and an
+//      open-addressing table there (a 32-bit CAS claims a slot for the entry
+//      that first brings a key, a 32-bit atomicMin keeps the smallest edge
 //      index of that key); every edge that is not its key's smallest index
 //      clears its bit in a survivor bitmap that starts all ones.  A bucket
 //      too large for shared memory (many copies of few keys) is listed and

@@ -50,7 +50,26 @@ size_t round16w(size_t words) { return (words + 3) & ~size_t(3); }
 // where the digits of the path's L levels are read as base-n0 numbers (both
 // < n0^L <= 2^32); the kernel appends a path as x = x * n0^L + digits, i.e.
 // x * (n0^L - 1) + x + digits, which keeps n0^L = 2^32 within 32 bits.
-// Header word g is the AA offset, 64 + g the P offset, 192 + g = b.
+// When the IDs fit 32 bits and the longest path's digits fit S bits with
+// 2S + 4 <= 32 (kron_packed_shift), packed arrays follow for the contract-case
+// kernel:
+//   A32[j] = (thr[j] << b) | alias[j]       (as in the compact R-MAT image)
+//   P32[j] = r | c << S | L << 2S           (row digits, column digits, L)
+//   PW[L]  = n0^L, L < 16
+//   MD[d]  = ceil(2^32 / n0^d), 1 <= d < 16: floor(x / n0^d) = umulhi(x, MD[d])
+//            for the digits x of a path of L >= d levels (x * n0^d < n0^2L <= 2^28)
+// Header word g is the AA offset, 64 + g the P offset, 128 the packed
+// arrays' offset (0 if absent), 192 + g = b.
+int kron_packed_shift(const rmat_table *t) {
+    const PathTable &g = t->groups[0];
+    if (wide_ids(t) || g.max_len > 15) return 0;
+    uint64_t v = 1;
+    for (int l = 0; l < g.max_len; ++l) v *= uint64_t(t->n0);
+    int S = 1;
+    while ((uint64_t(1) << S) < v) ++S;  // digits < n0^max_len <= 2^S
+    return 2 * S + 4 <= 32 ? S : 0;
+}
+
 rmat_status build_kron_image(rmat_table *t) {
     const PathTable &g = t->groups[0];
     const size_t N = size_t(1) << g.bits;
@@ -60,11 +79,15 @@ rmat_status build_kron_image(rmat_table *t) {
     d.ba_off_words = 0;
     d.bits = g.bits;
     d.len = g.max_len;
+    const int S = kron_packed_shift(t);
+    const size_t packed = round16w(d.bs_off_words + 4 * N);
+    d.ba_off_words = S ? uint32_t(packed) : 0u;
     t->format = kKron;
     t->gdesc.assign(1, d);
-    t->image.assign(round16w(d.bs_off_words + 4 * N), 0u);
+    t->image.assign(S ? packed + round16w(N) * 2 + 32 : packed, 0u);
     t->image[0] = d.a_off_words;
     t->image[kMaxGroups] = d.bs_off_words;
+    t->image[2 * kMaxGroups] = d.ba_off_words;
     t->image[3 * kMaxGroups] = uint32_t(g.bits);
     const uint32_t C = uint32_t((uint64_t(1) << 32) >> g.bits);
     const uint64_t n0 = uint64_t(t->n0);
@@ -85,6 +108,21 @@ rmat_status build_kron_image(rmat_table *t) {
         P[4 * j + 1] = uint32_t(c);
         P[4 * j + 2] = uint32_t(L);
         P[4 * j + 3] = uint32_t(pw - 1);
+        if (S) {
+            uint32_t *A32 = t->image.data() + d.ba_off_words;
+            uint32_t *P32 = A32 + round16w(N);
+            A32[j] = (g.thr[j] << g.bits) | g.alias[j];
+            P32[j] = uint32_t(r) | (uint32_t(c) << S) | (uint32_t(L) << (2 * S));
+        }
+    }
+    if (S) {
+        uint32_t *PW = t->image.data() + d.ba_off_words + 2 * round16w(N);
+        uint32_t *MD = PW + 16;
+        uint64_t v = 1;
+        for (int l = 0; l < 16; ++l, v *= n0) {
+            PW[l] = l <= g.max_len ? uint32_t(v) : 0u;
+            MD[l] = (l >= 1 && l <= g.max_len) ? uint32_t(((uint64_t(1) << 32) + v - 1) / v) : 0u;
+        }
     }
     return RMAT_OK;
 }

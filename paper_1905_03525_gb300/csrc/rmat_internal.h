@@ -65,6 +65,7 @@ struct AliasPlan {
     size_t smem_bytes = 0;
     void *kernel = nullptr;
     void *fast_kernel = nullptr;  // the contract-case kernel, when the table qualifies
+    size_t fast_smem_bytes = 0;   // its shared memory, when it differs from smem_bytes (Kronecker)
     unsigned *err = nullptr;
 };
 
@@ -108,6 +109,10 @@ int kron_max_k(int n0);       // largest k with n0^k <= 2^64
 uint32_t kron_symbol(uint64_t key, int n0, int level);
 // Whether the table's vertex IDs need 64 bits (n0^k > 2^32).
 bool wide_ids(const rmat_table *t);
+// Bits per coordinate of the packed Kronecker path (u32 IDs, digits of the
+// longest path in S bits, 2S + 4 <= 32, paths of at most 15 levels); 0 when the
+// table does not pack.
+int kron_packed_shift(const rmat_table *t);
 rmat_status build_fixed(const double *P_levels, int ell, PathTable &out);
 rmat_status normalise_params(const double in[4], double out[4]);
 

@@ -18,6 +18,10 @@
 //          CTA into shared memory by a TMA bulk copy on an mbarrier.
 // k_batch: many jobs in one persistent launch; CTAs pop work units from an
 //          atomic counter and restage the table when the job changes.
+// k_alias_fast: the contract case of k_alias (compact u32 tables in shared
+//          memory, four phase-1 draws, plain epilogue), whole tiles only.
+// k_kron / k_kron_fast: n0 x n0 initiators (Sec. 3); the fast kernel takes
+//          packed tables in k_alias_fast's shape.
 // k_naive: the plain R-MAT process (Sec. 1), one quadrant draw per level.
 #include <algorithm>
 #include <cstdio>
@@ -787,6 +791,133 @@ __global__ void __launch_bounds__(1024, 1) k_kron(const __grid_constant__ KronJo
     }
 }
 
+// Contract case of the Kronecker kernel: u32 IDs and paths that pack into one
+// word (P32 = r | c << S | L << 2S), with A32 = (thr << b) | alias as in the
+// compact R-MAT image and n0^L from a 16-word power table, all in shared
+// memory (8 bytes per column).  Phase 1 takes one Philox block and four draws
+// for every edge of a warp's tile, four edges per lane; the edges still short
+// of k levels continue, 32 at a time, on the next blocks; the tile leaves by
+// one bulk store.  The draws, the words they use and the arithmetic are those
+// of k_kron: keep column j iff u mod 2^(32-b) < thr[j] (the same test as
+// u < A[j] there), append x * n0^L + digits, and on the draw that passes k
+// levels keep the path's top k - filled digits (without a branch: every draw
+// takes min(L, k - filled) digits, dividing by n0^d with a 32-bit magic
+// multiplier, exact since digits x n0^d < 2^28).
+__global__ void __launch_bounds__(1024, 1) k_kron_fast(const __grid_constant__ KronJob J, int tile) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const unsigned char *>(J.blob) + J.c_off);
+        uint4 *dst = reinterpret_cast<uint4 *>(smem);
+        for (uint32_t i = threadIdx.x; i < J.c_bytes / 16; i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const uint32_t b = J.bits, N = 1u << b, shb = 32u - b, lowmask = (1u << shb) - 1u;  // 1 <= b <= 31
+    const uint32_t sA = dev::smem_u32(smem), sP = sA + 4u * ((N + 3u) & ~3u), sPW = sP + 4u * ((N + 3u) & ~3u);
+    const uint32_t sMD = sPW + 64u;
+    const uint32_t S = J.c_shift, rmask = (1u << S) - 1u, S2 = 2u * S;
+    const uint32_t uk = uint32_t(J.k);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t stage = sA + J.c_bytes + uint32_t(warp) * warp_region_bytes(false, false, tile);
+    const uint32_t p_fill = stage + 8u * uint32_t(tile), p_q = p_fill + uint32_t(tile);
+    const uint32_t iters = uint32_t(tile) / 32;
+    const uint64_t ntiles = J.count / uint64_t(tile);
+    auto draw = [&](uint32_t u, uint32_t &row, uint32_t &col, uint32_t &filled) {
+        const uint32_t j = u >> shb;
+        const uint32_t a = dev::lds32(sA + 4u * j);
+        const uint32_t sel = (u & lowmask) < (a >> b) ? j : (a & (N - 1u));
+        const uint32_t p = dev::lds32(sP + 4u * sel);
+        const uint32_t r = p & rmask, c = (p >> S) & rmask, L = p >> S2;
+        // the top `take` of the path's L digits: x div n0^(L - take), the
+        // whole path while it fits, nothing once the edge is full
+        const uint32_t take = min(L, uk - filled), d = L - take;
+        const uint32_t m = dev::lds32(sPW + 4u * take), md = dev::lds32(sMD + 4u * d);
+        row = row * m + (d ? __umulhi(r, md) : r);
+        col = col * m + (d ? __umulhi(c, md) : c);
+        filled += take;
+    };
+    bool issued = false;
+    for (uint64_t t = uint64_t(blockIdx.x) * nwarps + warp; t < ntiles; t += uint64_t(gridDim.x) * nwarps) {
+        const uint64_t first = t * uint64_t(tile);
+        const uint64_t ebase = J.e0 + first;
+        if (lane == 0 && issued) dev::bulk_wait_read_0();
+        __syncwarp();
+        // phase 1: one Philox block and four draws per edge, four edges per lane
+        uint32_t pm = 0;
+        for (uint32_t it = 0; it < iters; it += 4) {
+            uint4 w[4];
+            uint32_t row[4], col[4], filled[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint64_t e = ebase + (it + q) * 32 + lane;
+                w[q] = dev::philox_ks(0u, 0u, uint32_t(e), uint32_t(e >> 32), J.ks);
+                row[q] = col[q] = filled[q] = 0;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) draw(w[q].x, row[q], col[q], filled[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) draw(w[q].y, row[q], col[q], filled[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) draw(w[q].z, row[q], col[q], filled[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) draw(w[q].w, row[q], col[q], filled[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t idx = (it + q) * 32 + lane;
+                dev::sts64(stage + 8u * idx, row[q], col[q]);
+                dev::sts8(p_fill + idx, filled[q]);
+                pm |= uint32_t(filled[q] < uk) << (it + q);
+            }
+        }
+        // phase 2: the unfinished edges of the tile, 32 at a time
+        const uint32_t cnt = __popc(pm);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total) {
+            uint32_t pos = incl - cnt;
+            for (uint32_t m = pm; m; m &= m - 1) dev::sts16(p_q + 2u * pos++, (__ffs(m) - 1) * 32 + lane);
+            __syncwarp();
+            for (uint32_t pb = 0; pb < total; pb += 32) {
+                const bool has = pb + lane < total;
+                uint32_t row = 0, col = 0, filled = uk, idx = 0;
+                if (has) {
+                    idx = dev::lds16(p_q + 2u * (pb + lane));
+                    const uint2 v = dev::lds64(stage + 8u * idx);
+                    row = v.x;
+                    col = v.y;
+                    filled = dev::lds8(p_fill + idx);
+                }
+                const uint64_t e = ebase + idx;
+                for (uint32_t q = 1; q <= 17; ++q) {  // k <= 32 levels, >= 1 level a draw: at most 8 more blocks
+                    if (!__any_sync(0xffffffffu, filled < uk)) break;
+                    const uint4 w = dev::philox_ks(q, 0u, uint32_t(e), uint32_t(e >> 32), J.ks);
+                    draw(w.x, row, col, filled);
+                    if (!__any_sync(0xffffffffu, filled < uk)) break;
+                    draw(w.y, row, col, filled);
+                    if (!__any_sync(0xffffffffu, filled < uk)) break;
+                    draw(w.z, row, col, filled);
+                    if (!__any_sync(0xffffffffu, filled < uk)) break;
+                    draw(w.w, row, col, filled);
+                }
+                if (has) dev::sts64(stage + 8u * idx, row, col);
+            }
+        }
+        // the tile leaves by one bulk store
+        dev::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            dev::bulk_s2g_addr(reinterpret_cast<unsigned char *>(J.out) + first * 8u, stage, uint32_t(tile) * 8u);
+            dev::bulk_commit();
+        }
+        issued = true;
+    }
+    if (lane == 0 && issued) dev::bulk_wait_all();
+}
+
 // Order-independent checksum of the edges of every job of a step: the sum
 // mod 2^64 of mix(e, row, col) over the job's edges, where
 //   x = e * 0x9E3779B97F4A7C15 + row * 0xC2B2AE3D27D4EB4F + col * 0x165667B19E3779F9
@@ -980,12 +1111,26 @@ rmat_status plan_kron_launch(const rmat_table *t, const DeviceProps &props, Alia
     plan.smem_table = true;
     plan.threads = 1024;
     plan.tile = 0;
-    plan.smem_bytes = t->image.size() * 4;
+    const uint32_t packed_words = t->gdesc[0].ba_off_words;  // 0: no packed arrays
+    plan.smem_bytes = size_t(packed_words ? packed_words : t->image.size()) * 4;
     if (plan.smem_bytes > size_t(props.max_smem))
         return fail(RMAT_ERR_UNSUPPORTED, "Kronecker table larger than shared memory (use a smaller bound)");
     plan.kernel = u64 ? reinterpret_cast<void *>(&k_kron<true>) : reinterpret_cast<void *>(&k_kron<false>);
     cudaError_t e = set_smem_attr(plan.kernel, plan.smem_bytes);
     if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+    plan.fast_kernel = nullptr;
+    if (packed_words && !u64) {
+        const int tile = 512;
+        const size_t fast = (t->image.size() - packed_words) * 4 + 32 * size_t(warp_region_bytes(false, false, tile));
+        if (fast <= size_t(props.max_smem)) {
+            e = set_smem_attr(reinterpret_cast<void *>(&k_kron_fast), fast);
+            if (e != cudaSuccess)
+                return fail(RMAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+            plan.fast_kernel = reinterpret_cast<void *>(&k_kron_fast);
+            plan.fast_smem_bytes = fast;
+            plan.tile = tile;
+        }
+    }
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan.kernel, plan.threads, plan.smem_bytes);
     if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
@@ -1000,10 +1145,14 @@ rmat_status launch_kron(const rmat_table *t, const uint32_t *dblob, const AliasP
                         uint64_t e0, uint64_t count, void *out, cudaStream_t stream) {
     KronJob J{};
     J.blob = dblob;
-    J.blob_bytes = uint32_t(t->image.size() * 4);
+    J.blob_bytes = uint32_t(plan.smem_bytes);
     J.aa_off = 4u * t->gdesc[0].a_off_words;
     J.p_off = 4u * t->gdesc[0].bs_off_words;
     J.mulb = 1u << t->gdesc[0].bits;
+    J.c_off = 4u * t->gdesc[0].ba_off_words;
+    J.c_bytes = J.c_off ? uint32_t(t->image.size() * 4) - J.c_off : 0u;
+    J.c_shift = uint32_t(kron_packed_shift(t));
+    J.bits = uint32_t(t->gdesc[0].bits);
     J.k = t->k;
     const uint32_t k0 = uint32_t(seed), k1 = uint32_t(seed >> 32);
     for (int r = 0; r < 10; ++r) {
@@ -1023,6 +1172,25 @@ rmat_status launch_kron(const rmat_table *t, const uint32_t *dblob, const AliasP
     for (int d = 0; d <= 32; ++d) {
         J.mg[d] = (d >= 1 && D <= two32) ? uint64_t(((unsigned __int128)1 << 64) / D) + 1 : 0;
         D = D <= two32 ? D * uint64_t(t->n0) : D;
+    }
+    // The whole tiles of an aligned output go to the contract-case kernel when
+    // the table packs; the ragged tail (and every other case) to k_kron.
+    int tile = plan.tile;
+    if (plan.fast_kernel && count >= uint64_t(tile) && (reinterpret_cast<uintptr_t>(out) & 15u) == 0) {
+        const uint64_t nfull = count / uint64_t(tile);
+        KronJob F = J;
+        F.count = nfull * uint64_t(tile);
+        const uint64_t warps = plan.threads / 32;
+        const unsigned fgrid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>((nfull + warps - 1) / warps, plan.sms)));
+        void *fparams[] = {&F, &tile};
+        cudaError_t e = cudaLaunchKernel(plan.fast_kernel, dim3(fgrid), dim3(plan.threads), fparams,
+                                         plan.fast_smem_bytes, stream);
+        if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+        if (count == F.count) return RMAT_OK;
+        J.e0 += F.count;
+        J.count = count - F.count;
+        J.out = static_cast<unsigned char *>(out) + F.count * 8u;
+        count = J.count;
     }
     const uint64_t blocks = (count + plan.threads - 1) / plan.threads;
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(blocks, uint64_t(plan.sms) * plan.ctas_per_sm)));

@@ -74,10 +74,13 @@ struct BatchArgs {
 // One launch of the Kronecker kernel (n0 > 2): edges e0 .. e0+count-1.
 constexpr int kMaxKronK = 40;  // n0 >= 3: n0^k <= 2^64
 struct KronJob {
-    const uint32_t *blob;  // device image (header, AA, P)
-    uint32_t blob_bytes;
+    const uint32_t *blob;  // device image (header, AA, P, then the packed arrays when present)
+    uint32_t blob_bytes;     // bytes the general kernel stages (header, AA, P)
     uint32_t aa_off, p_off;  // byte offsets of AA and P in the image
     uint32_t mulb;           // 2^b: column j = umulhi(u, 2^b)
+    uint32_t c_off, c_bytes; // packed arrays (A32, P32, powers): byte offset and size; c_bytes = 0 if absent
+    uint32_t c_shift;        // bits per coordinate in a packed path
+    uint32_t bits;           // b
     int k;
     uint32_t ks[20];         // Philox round keys of the seed
     uint64_t e0, count;

@@ -278,7 +278,12 @@ def test_kron_table_matches_oracle(n0, k, kind, x):
     assert info["n0"] == n0
     assert info["index_bytes"] == (4 if n0 ** k <= 2 ** 32 else 8)
     N = 1 << ot.bits
-    assert info["device_image_bytes"] == 4 * (256 + 2 * N + 4 * N)
+    # packed arrays for the contract-case kernel (A32, P32, 16 powers, 16 magic
+    # divisors) when the
+    # IDs fit 32 bits and the longest path's digits fit S bits, 2S + 4 <= 32
+    S = max(1, (n0 ** int(ot.max_len) - 1).bit_length())
+    packs = n0 ** k <= 2 ** 32 and ot.max_len <= 15 and 2 * S + 4 <= 32
+    assert info["device_image_bytes"] == 4 * (256 + 2 * N + 4 * N + (2 * N + 32 if packs else 0))
 
 
 def test_kron_two_by_two_is_the_rmat_table():

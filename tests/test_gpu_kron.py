@@ -67,6 +67,25 @@ def test_kron_matches_oracle(n0, k, kind, x, m, e0):
     assert_same(pairs(out, wide), oracle.kron_generate(ot, k, 17, e0, m))
 
 
+def test_kron_bench_shape_through_both_kernels():
+    """The 3 x 3 bench table (k = 17, bound 4096): whole 512-edge tiles go to
+    the contract-case kernel and the ragged tail to the general one; an output
+    that is only 8-byte aligned takes the general kernel throughout.  Both
+    equal the oracle."""
+    from paper_1905_03525_gb300.workloads import KRON3
+    th = np.array(KRON3)
+    t, ot = rm.rmat_build_table_kron(th, 3, 17, 4096), oracle.KronTable.variable(th, 3, 17, 4096)
+    m, e0 = (1 << 20) + 77, 12345
+    ref = oracle.kron_generate(ot, 17, 1, e0, m)
+    out = rm.empty_edges_for(t, m + 1)
+    rm.rmat_generate(t, 1, e0, m, out[:m])
+    torch.cuda.synchronize()
+    assert_same(pairs(out[:m], False), ref)
+    rm.rmat_generate(t, 1, e0, m, out[1:])
+    torch.cuda.synchronize()
+    assert_same(pairs(out[1:], False), ref)
+
+
 def test_kron_host_output_and_chunks():
     t = rm.rmat_build_table_kron(THETA3, 3, 18, 1024)
     m = 200_001

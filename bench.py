@@ -603,7 +603,7 @@ def run_c4(args):
 
 def run_part(args):
     """Partitioned k = 26, m = 2^30 graph (Sec. 3): host divide and conquer
-    for the tile counts, then every tile in one persistent batched launch;
+    for the tile counts, then every tile in one persistent launch;
     the same graph size as the plain single launch beside it."""
     import torch
     import paper_1905_03525_gb300 as rm

@@ -337,8 +337,10 @@ rmat_status rmat_partition_tiles(const rmat_partition *p, uint64_t *tile_row, ui
 
 /* Generate this PE's edges into `out` (device, 8-byte aligned, `edges`
  * pairs of u32 for k <= 32, else u64), tile after tile in quadtree order, in
- * one persistent batched launch (asynchronous on `stream`).  The first call
- * for a given `out` prepares the launch (synchronous uploads); calls on one
+ * one persistent launch (asynchronous on `stream`): a dedicated kernel for
+ * u32 compact tables held in shared memory, the batched kernel otherwise.
+ * The first call (on a device, or for a given `out` on the batched path)
+ * prepares the launch (a synchronous upload of the tile list); calls on one
  * partition must not run concurrently, on the host or the device. */
 rmat_status rmat_generate_partition(rmat_partition *p, void *out, rmat_stream_t stream);
 

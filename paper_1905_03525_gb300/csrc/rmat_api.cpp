@@ -110,6 +110,11 @@ rmat_status fail(rmat_status st, const std::string &msg) {
     return st;
 }
 
+rmat_status plan_and_image(const rmat_table *t, AliasPlan &plan, const uint32_t **img) {
+    if (rmat_status st = get_plan(t, plan)) return st;
+    return ensure_device_copy(t, img);
+}
+
 void clear_error() { t_error.clear(); }
 
 rmat_status ensure_device_copy(const rmat_table *tc, const uint32_t **dptr) {

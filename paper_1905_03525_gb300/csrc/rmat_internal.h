@@ -121,5 +121,7 @@ rmat_status build_image(rmat_table *t);
 
 // Upload of the image for the current device (rmat_api.cu).
 rmat_status ensure_device_copy(const rmat_table *t, const uint32_t **dptr);
+// The table's launch plan on the current device (cached) and its device image.
+rmat_status plan_and_image(const rmat_table *t, AliasPlan &plan, const uint32_t **img);
 
 }  // namespace rmat

@@ -627,6 +627,144 @@ __global__ void __launch_bounds__(1024, 1) k_alias_fast(const __grid_constant__ 
     if (lane == 0 && issued) dev::bulk_wait_all();
 }
 
+// The tiles of a partitioned graph (Sec. 3) in k_alias_fast's shape: one
+// table and one seed for all of them, so the table is staged once and the
+// round keys come from the kernel parameters.  A warp takes a contiguous share
+// of the launch's warp tiles, finds the tile of its first by binary search and
+// walks the tile list forward from there;
+// the edges start from the tile's levels, then take four straight-line draws
+// (u32 accumulators ignore draws past k) and the usual second phase.  A
+// warp tile that ends its tile early runs guarded, and one whose output is
+// not 16-byte aligned leaves by plain coalesced stores instead of a bulk
+// store.
+__global__ void __launch_bounds__(1024, 1) k_part_fast(const __grid_constant__ Job J, const PartTile *tiles,
+                                                       uint32_t ntiles, uint64_t nwt, int tile) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(J.blob);
+        uint4 *dst = reinterpret_cast<uint4 *>(smem);
+        for (uint32_t i = threadIdx.x; i < J.blob_bytes / 16; i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const uint32_t sblob = dev::smem_u32(smem);
+    const dev::Group<true> G = group0<true>(J, sblob);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t stage = sblob + J.blob_bytes + uint32_t(warp) * warp_region_bytes(false, false, tile);
+    const uint32_t p_fill = stage + 8u * uint32_t(tile), p_q = p_fill + uint32_t(tile);
+    const uint32_t uk = uint32_t(J.k), sh = 32u - uk;
+    // this warp's contiguous share of the warp tiles, and the tile holding the first
+    const uint64_t gw = uint64_t(blockIdx.x) * nwarps + warp, all = uint64_t(gridDim.x) * nwarps;
+    const uint64_t w_begin = gw * nwt / all, w_end = (gw + 1) * nwt / all;
+    uint32_t j = 0;
+    for (uint32_t lo = 0, hi = ntiles; hi - lo > 1;) {  // the last tile with wt0 <= w_begin
+        const uint32_t mid = (lo + hi) / 2;
+        if (tiles[mid].wt0 <= w_begin) lo = mid;
+        else hi = mid;
+        j = lo;
+    }
+    bool issued = false;
+    for (uint64_t w = w_begin; w < w_end; ++w) {
+        while (j + 1 < ntiles && tiles[j + 1].wt0 <= w) ++j;
+        const PartTile &P = tiles[j];
+        const uint64_t first = (w - P.wt0) * uint64_t(tile);
+        const uint32_t n = uint32_t(min(uint64_t(tile), P.count - first));
+        const uint64_t ebase = P.e0 + first;
+        unsigned char *dst = reinterpret_cast<unsigned char *>(J.out) + (P.out + first) * 8u;
+        const uint32_t pr = P.pre_row, pc = P.pre_col, pl = P.pre_len;
+        if (lane == 0 && issued) dev::bulk_wait_read_0();
+        __syncwarp();
+        // phase 1: one Philox block and four draws per edge, four edges per lane
+        uint32_t pm = 0;
+        const uint32_t iters = (n + 31) / 32;
+        for (uint32_t it = 0; it < iters; it += 4) {
+            uint4 w4[4];
+            dev::Acc32 a[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint64_t e = ebase + (it + q) * 32 + lane;
+                w4[q] = dev::philox_ks(0u, 0u, uint32_t(e), uint32_t(e >> 32), J.ks);
+                a[q].row = pr;
+                a[q].col = pc;
+                a[q].filled = pl;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dev::draw<0, true>(G, w4[q].x, a[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dev::draw<0, true>(G, w4[q].y, a[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dev::draw<0, true>(G, w4[q].z, a[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dev::draw<0, true>(G, w4[q].w, a[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t idx = (it + q) * 32 + lane;
+                if (idx >= n) continue;
+                const bool done = a[q].filled >= uk;
+                dev::sts64(stage + 8u * idx, done ? a[q].row >> sh : a[q].row, done ? a[q].col >> sh : a[q].col);
+                dev::sts8(p_fill + idx, a[q].filled);
+                pm |= uint32_t(!done) << (it + q);
+            }
+        }
+        // phase 2: the unfinished edges of the warp tile, 32 at a time
+        const uint32_t cnt = __popc(pm);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total) {
+            uint32_t pos = incl - cnt;
+            for (uint32_t m = pm; m; m &= m - 1) dev::sts16(p_q + 2u * pos++, (__ffs(m) - 1) * 32 + lane);
+            __syncwarp();
+            for (uint32_t pb = 0; pb < total; pb += 32) {
+                const bool has = pb + lane < total;
+                dev::Acc32 acc;
+                acc.row = acc.col = 0;
+                acc.filled = uk;
+                uint32_t idx = 0;
+                if (has) {
+                    idx = dev::lds16(p_q + 2u * (pb + lane));
+                    const uint2 v = dev::lds64(stage + 8u * idx);
+                    acc.row = v.x;
+                    acc.col = v.y;
+                    acc.filled = dev::lds8(p_fill + idx);
+                }
+                const uint64_t e = ebase + idx;
+                for (uint32_t q = 1; q <= 17; ++q) {  // k <= 32 levels: at most 8 more blocks
+                    if (!__any_sync(0xffffffffu, acc.filled < uk)) break;
+                    const uint4 w = dev::philox_ks(q, 0u, uint32_t(e), uint32_t(e >> 32), J.ks);
+                    dev::draw<0, true>(G, w.x, acc);
+                    if (!__any_sync(0xffffffffu, acc.filled < uk)) break;
+                    dev::draw<0, true>(G, w.y, acc);
+                    if (!__any_sync(0xffffffffu, acc.filled < uk)) break;
+                    dev::draw<0, true>(G, w.z, acc);
+                    if (!__any_sync(0xffffffffu, acc.filled < uk)) break;
+                    dev::draw<0, true>(G, w.w, acc);
+                }
+                if (has) dev::sts64(stage + 8u * idx, acc.row >> sh, acc.col >> sh);
+            }
+        }
+        if (n == uint32_t(tile) && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+            // a whole, aligned warp tile leaves by one bulk store
+            dev::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                dev::bulk_s2g_addr(dst, stage, uint32_t(tile) * 8u);
+                dev::bulk_commit();
+            }
+            issued = true;
+        } else {
+            __syncwarp();
+            uint2 *o = reinterpret_cast<uint2 *>(dst);
+            for (uint32_t i = lane; i < n; i += 32) o[i] = dev::lds64(stage + 8u * i);
+            __syncwarp();
+        }
+    }
+    if (lane == 0 && issued) dev::bulk_wait_all();
+}
+
 // One work unit of a batch: edges [u * unit_edges, ...) of job unit_job[u].
 template <bool U64, int FMT, bool SMEM, bool LEVELS, int EPI, bool PRE>
 __device__ __forceinline__ void batch_unit(const Job &J, const Scramble &S, SharedKeys ks, uint32_t sblob,
@@ -1255,6 +1393,7 @@ rmat_status plan_alias_launch(const rmat_table *t, const rmat_launch_config_t &w
                            : nullptr;
     cudaError_t e = set_smem_attr(plan.kernel, plan.smem_bytes);
     if (e == cudaSuccess && plan.fast_kernel) e = set_smem_attr(plan.fast_kernel, plan.smem_bytes);
+    if (e == cudaSuccess && plan.fast_kernel) e = set_smem_attr(reinterpret_cast<void *>(&k_part_fast), plan.smem_bytes);
     if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan.kernel, threads, plan.smem_bytes);
@@ -1316,6 +1455,23 @@ Scramble make_scramble(const rmat_table *t) {
     }
     S.mask = (wmask << s) & wmask;
     return S;
+}
+
+rmat_status launch_partition_fast(const rmat_table *t, const uint32_t *dblob, const AliasPlan &plan, uint64_t seed,
+                                  const PartTile *tiles, uint32_t ntiles, uint64_t nwt, void *out,
+                                  cudaStream_t stream) {
+    if (nwt == 0) return RMAT_OK;
+    if (!plan.fast_kernel) return fail(RMAT_ERR_UNSUPPORTED, "table does not take the contract-case kernel");
+    Job J = make_job(t, dblob, true, seed, 0, 0, out);
+    int tile = plan.tile;
+    const uint64_t warps = uint64_t(plan.threads / 32);
+    const uint64_t max_ctas = uint64_t(plan.sms) * plan.ctas_per_sm;
+    const unsigned grid = unsigned(std::max<uint64_t>(1, std::min((nwt + warps - 1) / warps, max_ctas)));
+    void *params[] = {&J, &tiles, &ntiles, &nwt, &tile};
+    cudaError_t e = cudaLaunchKernel(reinterpret_cast<void *>(&k_part_fast), dim3(grid), dim3(plan.threads), params,
+                                     plan.smem_bytes, stream);
+    if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return RMAT_OK;
 }
 
 rmat_status launch_alias(const rmat_table *t, const uint32_t *dblob, const AliasPlan &plan, uint64_t seed,

@@ -41,6 +41,15 @@ struct Job {
     uint32_t pre_len;
 };
 
+// One tile of a partitioned graph for the contract-case partition kernel:
+// its edges e0 .. e0 + count - 1 go to output slots out .. out + count - 1
+// (edges from the start of the PE's output), in warp tiles wt0, wt0 + 1, ...
+// of the launch; pre_* are the tile's levels, left-aligned in 32 bits.
+struct PartTile {
+    uint64_t e0, out, count, wt0;
+    uint32_t pre_row, pre_col, pre_len, pad;
+};
+
 // Vertex relabelling constants of a job (used when flags & kScrambleFlag),
 // in the form the kernels apply them: to an identifier held left-aligned in a
 // W-bit word (W = 32 for k <= 32, else 64), s = W - k.  m[i] is the round's
@@ -100,6 +109,12 @@ Scramble make_scramble(const rmat_table *t);
 // Start every edge of a batched job inside tile (R, C) of a depth-`levels`
 // partition: the tile's levels are fixed, the draws fill the other k - levels.
 void set_tile_prefix(Job &J, const rmat_table *t, int levels, uint64_t R, uint64_t C);
+// Every tile of a partition (u32 compact tables that take k_alias_fast) in one
+// launch of k_part_fast; `tiles` (device, ntiles entries, non-empty tiles in
+// output order) cover nwt warp tiles of plan.tile edges.
+rmat_status launch_partition_fast(const rmat_table *t, const uint32_t *dblob, const AliasPlan &plan, uint64_t seed,
+                                  const PartTile *tiles, uint32_t ntiles, uint64_t nwt, void *out,
+                                  cudaStream_t stream);
 rmat_status launch_alias(const rmat_table *t, const uint32_t *dblob, const AliasPlan &plan, uint64_t seed,
                          uint64_t e0, uint64_t count, void *out, cudaStream_t stream);
 size_t warp_bytes(bool u64, bool levels, int tile);

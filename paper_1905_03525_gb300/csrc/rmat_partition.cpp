@@ -10,7 +10,9 @@
 // is then generated by the sampling kernel with the tile's t levels fixed
 // (a batched job per tile), which keeps every edge of a PE's rows on that PE.
 //
-// Host side only; the per-tile generation runs in k_batch (rmat_kernels.cu).
+// Host side only; the per-tile generation runs in k_part_fast when the table
+// takes the contract-case kernel (u32 compact tables in shared memory), else
+// in k_batch (rmat_kernels.cu).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -28,6 +30,10 @@ struct rmat_partition {
     uint64_t edges = 0;
     rmat_batch *batch = nullptr;  // prepared for `batch_out`
     void *batch_out = nullptr;
+    rmat::PartTile *dtiles = nullptr;  // the contract-case kernel's tile list, on device `dtiles_dev`
+    int dtiles_dev = -1, dtile = 0;    // ... for warp tiles of `dtile` edges
+    uint32_t ntiles = 0;
+    uint64_t nwt = 0;
 };
 
 namespace rmat {
@@ -253,6 +259,52 @@ rmat_status rmat_generate_partition(rmat_partition *p, void *out, rmat_stream_t 
     if (p->edges == 0) return RMAT_OK;
     if (!out) return fail(RMAT_ERR_INVALID_ARGUMENT, "output pointer is NULL");
     if (reinterpret_cast<uintptr_t>(out) & 7u) return fail(RMAT_ERR_INVALID_ARGUMENT, "output must be 8-byte aligned");
+    AliasPlan plan;
+    const uint32_t *img = nullptr;
+    if (rmat_status st = plan_and_image(p->t, plan, &img)) return st;
+    if (plan.fast_kernel && plan.fmt == kCompact && !plan.u64 && !plan.levels) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+        if (!p->dtiles || p->dtiles_dev != dev || p->dtile != plan.tile) {
+            if (p->dtiles) cudaFree(p->dtiles);
+            p->dtiles = nullptr;
+            std::vector<PartTile> v;
+            uint64_t at = 0, wt = 0;
+            for (size_t i = 0; i < p->row.size(); ++i) {
+                if (p->count[i]) {
+                    Job J{};
+                    set_tile_prefix(J, p->t, p->levels, p->row[i], p->col[i]);
+                    PartTile P{};
+                    P.e0 = p->first[i];
+                    P.out = at;
+                    P.count = p->count[i];
+                    P.wt0 = wt;
+                    P.pre_row = uint32_t(J.pre_row);
+                    P.pre_col = uint32_t(J.pre_col);
+                    P.pre_len = J.pre_len;
+                    v.push_back(P);
+                    wt += (p->count[i] + uint64_t(plan.tile) - 1) / uint64_t(plan.tile);
+                }
+                at += p->count[i];
+            }
+            e = cudaMalloc(&p->dtiles, v.size() * sizeof(PartTile));
+            if (e == cudaSuccess) e = cudaMemcpy(p->dtiles, v.data(), v.size() * sizeof(PartTile), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                if (p->dtiles) cudaFree(p->dtiles);
+                p->dtiles = nullptr;
+                cudaGetLastError();
+                return fail(e == cudaErrorMemoryAllocation ? RMAT_ERR_OUT_OF_MEMORY : RMAT_ERR_CUDA,
+                            std::string("partition tile list: ") + cudaGetErrorString(e));
+            }
+            p->dtiles_dev = dev;
+            p->dtile = plan.tile;
+            p->ntiles = uint32_t(v.size());
+            p->nwt = wt;
+        }
+        return launch_partition_fast(p->t, img, plan, p->seed, p->dtiles, p->ntiles, p->nwt, out,
+                                     reinterpret_cast<cudaStream_t>(stream));
+    }
     if (!p->batch || p->batch_out != out) {
         rmat_batch_free(p->batch);
         p->batch = nullptr;
@@ -283,6 +335,7 @@ rmat_status rmat_generate_partition(rmat_partition *p, void *out, rmat_stream_t 
 void rmat_free_partition(rmat_partition *p) {
     if (!p) return;
     rmat_batch_free(p->batch);
+    if (p->dtiles) cudaFree(p->dtiles);
     delete p;
 }
 

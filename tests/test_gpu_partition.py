@@ -42,6 +42,7 @@ def assert_same(gpu, ref):
     ("variable", G500, 40, 5, 60_000, 5, None),            # u64 output
     ("variable", G500, 14, 14, 5_000, 6, None),            # tiles of one cell: no draws
     ("variable", G500, 26, 2, 1, 7, None),                 # a single edge
+    ("variable", G500, 26, 5, 2_000_003, 9, (3, 20)),      # the bench's tiles, one PE's rows
 ])
 def test_partition_matches_oracle(kind, params, k, t, m, seed, rows):
     table = rm.rmat_build_table(*params, k, 4096) if kind == "variable" else rm.rmat_build_table_fixed(*params, k, 4)

@@ -54,7 +54,7 @@ struct rmat_batch {
     std::vector<Entry> entries;
     bool prepared = false;
     int device = -1;
-    Side side[2];
+    Side side[3];  // u32 jobs for k_batch_fast, other u32 jobs, u64 jobs
     rmat_launch_config_t cfg{1024, 1, 512};
     bool cfg_set = false;  // else the tile adapts to the tables (prepare_side)
     uint64_t edges = 0;
@@ -77,11 +77,27 @@ rmat_status dev_alloc(T **p, size_t bytes) {
     return RMAT_OK;
 }
 
-rmat_status prepare_side(rmat_batch *b, bool u64, const DeviceProps &props, Side &s) {
+// Whether a u32 entry runs in k_batch_fast: a whole graph (no tile prefix),
+// compact paths, one table for all levels, plain epilogue, and a table that
+// fits in shared memory beside the warps' tiles of the batch's shape.
+bool fast_entry(const rmat_batch *b, const rmat_batch::Entry &en, const DeviceProps &props) {
+    const rmat_table *t = en.t;
+    if (t->k > 32 || en.tile_levels || t->format != kCompact || t->per_level || t->flags || t->scramble) return false;
+    const int threads = std::max(128, std::min(1024, b->cfg.threads / 32 * 32));
+    const int tile = std::max(32, std::min(1024, b->cfg.tile_edges / 32 * 32));
+    return kBatchHeaderBytes + size_t(threads / 32) * warp_bytes(false, false, tile) + t->image.size() * 4 <=
+           size_t(props.max_smem);
+}
+
+// kind 0: the u32 entries that take k_batch_fast; 1: the other u32 entries;
+// 2: the u64 entries.  Each kind is one launch.
+rmat_status prepare_side(rmat_batch *b, int kind, const DeviceProps &props, Side &s) {
+    const bool u64 = kind == 2;
     s.u64 = u64;
     std::vector<const rmat_batch::Entry *> mine;
     for (const auto &en : b->entries)
-        if ((en.t->k > 32) == u64 && en.count) mine.push_back(&en);
+        if ((en.t->k > 32) == u64 && en.count && (u64 || fast_entry(b, en, props) == (kind == 0)))
+            mine.push_back(&en);
     if (mine.empty()) return RMAT_OK;
 
     int threads = std::max(128, std::min(1024, b->cfg.threads / 32 * 32));
@@ -175,6 +191,11 @@ rmat_status prepare_side(rmat_batch *b, bool u64, const DeviceProps &props, Side
     s.args.tile = tile;
     s.args.err = props.err;
     for (const Job &J : jobs) s.args.general |= (J.pre_len || (J.flags & kScrambleFlag)) ? 1 : 0;
+    // whole graphs with u32 IDs, compact tables in shared memory and the plain
+    // epilogue take the lean kernel (k_batch_fast)
+    bool fast = kind == 0;
+    for (const Job &J : jobs) fast = fast && J.smem && J.draws1 >= 1 && J.draws1 <= 4;
+    s.args.fast = fast ? 1 : 0;
     return RMAT_OK;
 }
 
@@ -247,8 +268,8 @@ rmat_status rmat_batch_prepare(rmat_batch *b, const rmat_launch_config_t *cfg) {
     if (rmat_status st = device_props(props)) return st;
     for (Side &s : b->side) free_side(s);
     b->prepared = false;
-    for (int u = 0; u < 2; ++u)
-        if (rmat_status st = prepare_side(b, u == 1, props, b->side[u])) {
+    for (int u = 0; u < 3; ++u)
+        if (rmat_status st = prepare_side(b, u, props, b->side[u])) {
             for (Side &s : b->side) free_side(s);
             return st;
         }

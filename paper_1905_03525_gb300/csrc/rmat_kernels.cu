@@ -869,6 +869,190 @@ __global__ void __launch_bounds__(1024) k_batch(BatchArgs B) {
     if (lane == 0 && W.issued) dev::bulk_wait_all();
 }
 
+// One warp tile of k_batch_fast: phase 1 takes one Philox block and D draws
+// for four edges per lane (the job's draws1, known per job), the unfinished
+// edges finish 32 at a time, and the tile leaves by a bulk store when its
+// output is 16-byte aligned (by plain stores otherwise).  FULL: the tile holds
+// W.tile edges, a multiple of 128.
+template <int D, bool FULL>
+__device__ __forceinline__ void fast_batch_tile(const Job &J, const dev::Group<true> &G, SharedKeys ks,
+                                                uint64_t first, uint32_t n, WarpState &W) {
+    const int lane = W.lane;
+    const uint32_t uk = uint32_t(J.k), sh = 32u - uk;
+    const uint32_t stage = W.region, p_fill = stage + 8u * uint32_t(W.tile), p_q = p_fill + uint32_t(W.tile);
+    const uint64_t ebase = J.e0 + first;
+    if (lane == 0 && W.issued) dev::bulk_wait_read_0();
+    __syncwarp();
+    uint32_t pm = 0;
+    const uint32_t iters = (n + 31) / 32;
+    for (uint32_t it = 0; it < iters; it += 4) {
+        uint4 w[4];
+        dev::Acc32 a[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] = edge_block(ks, 0u, ebase + (it + q) * 32 + lane);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dev::draw<0, true, true>(G, w[q].x, a[q]);
+        if constexpr (D >= 2) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dev::draw<0, true>(G, w[q].y, a[q]);
+        }
+        if constexpr (D >= 3) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dev::draw<0, true>(G, w[q].z, a[q]);
+        }
+        if constexpr (D >= 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dev::draw<0, true>(G, w[q].w, a[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t idx = (it + q) * 32 + lane;
+            if (!FULL && idx >= n) continue;
+            const bool done = a[q].filled >= uk;
+            dev::sts64(stage + 8u * idx, done ? a[q].row >> sh : a[q].row, done ? a[q].col >> sh : a[q].col);
+            dev::sts8(p_fill + idx, a[q].filled);
+            pm |= uint32_t(!done) << (it + q);
+        }
+    }
+    const uint32_t cnt = __popc(pm);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total) {
+        uint32_t pos = incl - cnt;
+        for (uint32_t m = pm; m; m &= m - 1) dev::sts16(p_q + 2u * pos++, (__ffs(m) - 1) * 32 + lane);
+        __syncwarp();
+        for (uint32_t pb = 0; pb < total; pb += 32) {
+            const bool has = pb + lane < total;
+            dev::Acc32 acc;
+            acc.row = acc.col = 0;
+            acc.filled = uk;
+            uint32_t idx = 0;
+            if (has) {
+                idx = dev::lds16(p_q + 2u * (pb + lane));
+                const uint2 v = dev::lds64(stage + 8u * idx);
+                acc.row = v.x;
+                acc.col = v.y;
+                acc.filled = dev::lds8(p_fill + idx);
+            }
+            const uint64_t e = ebase + idx;
+            // the remaining words of block 0, then blocks 1, 2, ...
+            if constexpr (D < 4) {
+                const uint4 w = edge_block(ks, 0u, e);
+                if (D < 2 && __any_sync(0xffffffffu, acc.filled < uk)) dev::draw<0, true>(G, w.y, acc);
+                if (D < 3 && __any_sync(0xffffffffu, acc.filled < uk)) dev::draw<0, true>(G, w.z, acc);
+                if (__any_sync(0xffffffffu, acc.filled < uk)) dev::draw<0, true>(G, w.w, acc);
+            }
+            for (uint32_t q = 1; q <= 17; ++q) {  // k <= 32 levels: at most 8 more blocks
+                if (!__any_sync(0xffffffffu, acc.filled < uk)) break;
+                const uint4 w = edge_block(ks, q, e);
+                dev::draw<0, true>(G, w.x, acc);
+                if (!__any_sync(0xffffffffu, acc.filled < uk)) break;
+                dev::draw<0, true>(G, w.y, acc);
+                if (!__any_sync(0xffffffffu, acc.filled < uk)) break;
+                dev::draw<0, true>(G, w.z, acc);
+                if (!__any_sync(0xffffffffu, acc.filled < uk)) break;
+                dev::draw<0, true>(G, w.w, acc);
+            }
+            if (has) dev::sts64(stage + 8u * idx, acc.row >> sh, acc.col >> sh);
+        }
+    }
+    unsigned char *gdst = reinterpret_cast<unsigned char *>(J.out) + first * 8u;
+    const uint32_t bytes = n * 8u;
+    if (((reinterpret_cast<uintptr_t>(gdst) | bytes) & 15u) == 0) {
+        dev::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            dev::bulk_s2g_addr(gdst, stage, bytes);
+            dev::bulk_commit();
+        }
+        W.issued = true;
+    } else {
+        __syncwarp();
+        uint2 *dst = reinterpret_cast<uint2 *>(gdst);
+        for (uint32_t i = lane; i < n; i += 32) dst[i] = dev::lds64(stage + 8u * i);
+        __syncwarp();
+    }
+}
+
+// Batches of whole graphs with u32 IDs, compact tables in shared memory and
+// the plain epilogue (rmat_batch_prepare gathers such jobs into a launch of
+// their own): k_batch's work units and table restaging, with k_alias_fast's
+// sampling loop (four edges per lane; phase-1 draws specialised per job) and
+// the round keys in shared memory.  Without k_batch's sixteen table variants
+// the loop has the registers for four edges per lane.
+__global__ void __launch_bounds__(1024, 1) k_batch_fast(BatchArgs B) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
+    unsigned long long *s_unit = reinterpret_cast<unsigned long long *>(smem + 8);
+    uint32_t *s_ks = reinterpret_cast<uint32_t *>(smem + 16);
+    unsigned char *s_blob = smem + kBatchHeaderBytes;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const uint32_t sblob = dev::smem_u32(s_blob);
+    const SharedKeys ks{dev::smem_u32(s_ks)};
+    if (threadIdx.x == 0) {
+        dev::mbar_init(mbar, 1);
+        dev::fence_mbar_init();
+    }
+    WarpState W;
+    W.region = sblob + B.max_blob_bytes + uint32_t(warp) * warp_region_bytes(false, false, B.tile);
+    W.tile = B.tile;
+    W.issued = false;
+    W.lane = lane;
+    const bool whole = B.tile % 128 == 0;
+    const Job *staged = nullptr;
+    uint32_t parity = 0;
+    unsigned long long next = 0;
+    if (threadIdx.x == 0) next = atomicAdd(B.counter, 1ull);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            *s_unit = next;
+            if (next < B.units) next = atomicAdd(B.counter, 1ull);
+        }
+        __syncthreads();
+        const unsigned long long unit = *s_unit;
+        if (unit >= B.units) break;
+        const Job *jp = B.jobs + B.unit_job[unit];
+        if (jp != staged) {
+            if (threadIdx.x < 20) s_ks[threadIdx.x] = jp->ks[threadIdx.x];
+            if (!stage_blob(s_blob, jp->blob, jp->blob_bytes, mbar, parity)) {  // (its barrier publishes s_ks)
+                if (threadIdx.x == 0) {
+                    atomicOr(B.err, 1u);
+                    dev::mbar_wait_bounded(mbar, parity, kWaitLimit);
+                }
+                break;
+            }
+            parity ^= 1u;
+            staged = jp;
+        }
+        const Job &J = *jp;
+        const dev::Group<true> G = group0<true>(J, sblob);
+        const uint64_t f0 = (unit - J.unit_begin) * B.unit_edges;
+        const uint64_t end = min(J.count, f0 + B.unit_edges);
+        const int d = J.draws1;
+        for (uint64_t first = f0 + uint64_t(warp) * W.tile; first < end; first += uint64_t(nwarps) * W.tile) {
+            const uint32_t n = uint32_t(min(uint64_t(W.tile), end - first));
+            const bool full = whole && n == uint32_t(W.tile);
+#define RMAT_FAST_TILE(DD)                                          \
+    if (full) fast_batch_tile<DD, true>(J, G, ks, first, n, W);     \
+    else fast_batch_tile<DD, false>(J, G, ks, first, n, W);
+            if (d >= 4) { RMAT_FAST_TILE(4) }
+            else if (d == 3) { RMAT_FAST_TILE(3) }
+            else if (d == 2) { RMAT_FAST_TILE(2) }
+            else { RMAT_FAST_TILE(1) }
+#undef RMAT_FAST_TILE
+        }
+        __syncthreads();  // s_unit and the staged table are reused next round
+    }
+    if (lane == 0 && W.issued) dev::bulk_wait_all();
+}
+
 // Stochastic Kronecker graphs with an n0 x n0 initiator, n0 > 2 (Sec. 3).
 // One edge per thread over a persistent grid: the table (AA = {A, alias},
 // P = {row digits, column digits, L, n0^L - 1}) is staged in shared memory,
@@ -1555,7 +1739,11 @@ rmat_status load_batch_kernels() {
 }
 
 rmat_status launch_batch(bool u64, const BatchArgs &args, int grid, int threads, size_t smem, cudaStream_t stream) {
-    void *fn = batch_kernel(u64, args.general != 0);
+    void *fn = (!u64 && args.fast) ? reinterpret_cast<void *>(&k_batch_fast) : batch_kernel(u64, args.general != 0);
+    if (!u64 && args.fast) {
+        const cudaError_t ea = set_smem_attr(fn, smem);
+        if (ea != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ea));
+    }
     cudaError_t e = cudaMemsetAsync(args.counter, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     BatchArgs a = args;

@@ -78,6 +78,7 @@ struct BatchArgs {
     int tile;
     unsigned *err;
     int general;               // some job is a partition tile (pre_len > 0) or relabels IDs
+    int fast;                  // every job takes k_batch_fast (u32 compact shared-memory tables, plain epilogue)
 };
 
 // One launch of the Kronecker kernel (n0 > 2): edges e0 .. e0+count-1.

@@ -40,12 +40,14 @@ FALLBACK_HBM_GBS = 6800.0
 # dram__bytes_write.sum`, 1 pass, profiles/k_alias_fast_k26_m2p28_traffic.md)
 # scaled by the edges (x4); valid only for the kernel sources whose hash is
 # recorded with it.
-TRAFFIC = {"kernel_sha256_16": "0b212d8113454048", "bytes_per_launch": 4 * (968192 + 2085514752),
+TRAFFIC = {"kernel_sha256_16": "35fedf31c18221e1", "bytes_per_launch": 4 * (460032 + 2086046464),
            "source": "m=2^28 capture scaled x4 (profiles/k_alias_fast_k26_m2p28_traffic.md)"}
 # Warp instructions per edge of the same kernel (smsp__inst_executed.sum / 2^26 on
 # the m=2^26 `ncu --set full` capture of this workload; ALU-pipe instructions from
-# smsp__inst_executed_pipe_alu.sum on the same case), valid for the same hash.
-INSTR = {"kernel_sha256_16": "0b212d8113454048", "warp_instr_per_edge": 293341562 / 2 ** 26,
+# smsp__inst_executed_pipe_alu.sum on the same case, an earlier build of the same
+# kernel code: identical total instruction count and ALU-pipe share), valid for
+# the same hash.
+INSTR = {"kernel_sha256_16": "35fedf31c18221e1", "warp_instr_per_edge": 293341562 / 2 ** 26,
          "alu_warp_instr_per_edge": 71.1 / 32}
 KERNEL_SOURCES = ("paper_1905_03525_gb300/csrc/rmat_device.cuh", "paper_1905_03525_gb300/csrc/rmat_kernels.cu")
 

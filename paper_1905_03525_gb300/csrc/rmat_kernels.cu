@@ -19,7 +19,8 @@
 // k_batch: many jobs in one persistent launch; CTAs pop work units from an
 //          atomic counter and restage the table when the job changes.
 // k_alias_fast: the contract case of k_alias (compact u32 tables in shared
-//          memory, four phase-1 draws, plain epilogue), whole tiles only.
+//          memory, four phase-1 draws, plain or relabelling epilogue), whole
+//          tiles only.
 // k_kron / k_kron_fast: n0 x n0 initiators (Sec. 3); the fast kernel takes
 //          packed tables in k_alias_fast's shape.
 // k_naive: the plain R-MAT process (Sec. 1), one quadrant draw per level.
@@ -525,7 +526,9 @@ __global__ void __launch_bounds__(1024, 1) k_alias(const __grid_constant__ Job J
 // that bound this kernel -- shifts with any other code in the kernel (the
 // general kernel's ragged-tile and unaligned-store paths cost ~5 %).  The host
 // sends everything else, and the ragged tail of a launch, to k_alias.
-__global__ void __launch_bounds__(1024, 1) k_alias_fast(const __grid_constant__ Job J, int tile) {
+template <bool SCR>
+__global__ void __launch_bounds__(1024, 1) k_alias_fast(const __grid_constant__ Job J,
+                                                        const __grid_constant__ Scramble S, int tile) {
     extern __shared__ __align__(128) unsigned char smem[];
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(J.blob);
@@ -569,7 +572,12 @@ __global__ void __launch_bounds__(1024, 1) k_alias_fast(const __grid_constant__ 
             for (int q = 0; q < 4; ++q) {
                 const uint32_t idx = (it + q) * 32 + lane;
                 const bool done = a[q].filled >= uk;
-                dev::sts64(stage + 8u * idx, done ? a[q].row >> sh : a[q].row, done ? a[q].col >> sh : a[q].col);
+                uint32_t r = done ? a[q].row >> sh : a[q].row, c = done ? a[q].col >> sh : a[q].col;
+                if (SCR && done) {  // relabelled IDs (Sec. 3 scrambling), fused into the store
+                    r = uint32_t(scramble_id<false>(a[q].row, J, S));
+                    c = uint32_t(scramble_id<false>(a[q].col, J, S));
+                }
+                dev::sts64(stage + 8u * idx, r, c);
                 dev::sts8(p_fill + idx, a[q].filled);
                 pm |= uint32_t(!done) << (it + q);
             }
@@ -612,7 +620,13 @@ __global__ void __launch_bounds__(1024, 1) k_alias_fast(const __grid_constant__ 
                     if (!__any_sync(0xffffffffu, acc.filled < uk)) break;
                     dev::draw<0, true>(G, w.w, acc);
                 }
-                if (has) dev::sts64(stage + 8u * idx, acc.row >> sh, acc.col >> sh);
+                if (has) {
+                    if (SCR)
+                        dev::sts64(stage + 8u * idx, uint32_t(scramble_id<false>(acc.row, J, S)),
+                                   uint32_t(scramble_id<false>(acc.col, J, S)));
+                    else
+                        dev::sts64(stage + 8u * idx, acc.row >> sh, acc.col >> sh);
+                }
             }
         }
         // the tile leaves by one bulk store
@@ -1572,9 +1586,12 @@ rmat_status plan_alias_launch(const rmat_table *t, const rmat_launch_config_t &w
     const int d4 = phase1_draws(t) == 4 ? 1 : 0;
     const int epi = ((t->flags & RMAT_UNDIRECTED) ? kEpiUndir : 0) | (t->scramble ? kEpiScr : 0);
     plan.kernel = alias_kernel_table[d4][plan.fmt][u64][smem_table][levels][epi]();
-    plan.fast_kernel = (d4 && plan.fmt == kCompact && !u64 && smem_table && !levels && epi == 0)
-                           ? reinterpret_cast<void *>(&k_alias_fast)
-                           : nullptr;
+    // the contract case: compact u32 tables in shared memory, four phase-1
+    // draws, the plain epilogue or relabelling alone
+    plan.fast_kernel = !(d4 && plan.fmt == kCompact && !u64 && smem_table && !levels) ? nullptr
+                       : epi == 0        ? reinterpret_cast<void *>(&k_alias_fast<false>)
+                       : epi == kEpiScr  ? reinterpret_cast<void *>(&k_alias_fast<true>)
+                                         : nullptr;
     cudaError_t e = set_smem_attr(plan.kernel, plan.smem_bytes);
     if (e == cudaSuccess && plan.fast_kernel) e = set_smem_attr(plan.fast_kernel, plan.smem_bytes);
     if (e == cudaSuccess && plan.fast_kernel) e = set_smem_attr(reinterpret_cast<void *>(&k_part_fast), plan.smem_bytes);
@@ -1681,7 +1698,7 @@ rmat_status launch_alias(const rmat_table *t, const uint32_t *dblob, const Alias
         Job F = J;
         F.count = nfull * uint64_t(tile);
         const unsigned grid = unsigned(std::max<uint64_t>(1, std::min((nfull + warps - 1) / warps, max_ctas)));
-        void *params[] = {&F, &tile};
+        void *params[] = {&F, &S, &tile};
         cudaError_t e =
             cudaLaunchKernel(plan.fast_kernel, dim3(grid), dim3(plan.threads), params, plan.smem_bytes, stream);
         if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));

@@ -262,7 +262,7 @@ rmat_status rmat_generate_partition(rmat_partition *p, void *out, rmat_stream_t 
     AliasPlan plan;
     const uint32_t *img = nullptr;
     if (rmat_status st = plan_and_image(p->t, plan, &img)) return st;
-    if (plan.fast_kernel && plan.fmt == kCompact && !plan.u64 && !plan.levels) {
+    if (plan.fast_kernel && plan.fmt == kCompact && !plan.u64 && !plan.levels && !p->t->flags && !p->t->scramble) {
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));

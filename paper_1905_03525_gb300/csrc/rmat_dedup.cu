@@ -111,8 +111,19 @@ __global__ void __launch_bounds__(kBlock) k_dd_hist(const uint2 *edges, uint64_t
     const uint32_t nb = 1u << bits;
     for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) h[b] = 0;
     __syncthreads();
-    for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x)
-        atomicAdd(&h[top_bits(mix64(edge_key(edges, i, k)), bits)], 1u);
+    // four edges per thread in flight
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t i0 = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i0 < n; i0 += 4 * stride) {
+        uint64_t key[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint64_t i = i0 + u * stride;
+            key[u] = i < n ? edge_key(edges, i, k) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (i0 + u * stride < n) atomicAdd(&h[top_bits(mix64(key[u]), bits)], 1u);
+    }
     __syncthreads();
     for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
         if (h[b]) atomicAdd(&counts[b], h[b]);

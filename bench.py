@@ -40,15 +40,13 @@ FALLBACK_HBM_GBS = 6800.0
 # dram__bytes_write.sum`, 1 pass, profiles/k_alias_fast_k26_m2p28_traffic.md)
 # scaled by the edges (x4); valid only for the kernel sources whose hash is
 # recorded with it.
-TRAFFIC = {"kernel_sha256_16": "35fedf31c18221e1", "bytes_per_launch": 4 * (460032 + 2086046464),
+TRAFFIC = {"kernel_sha256_16": "e2a6c8914b67d5b0", "bytes_per_launch": 4 * (123904 + 2086040064),
            "source": "m=2^28 capture scaled x4 (profiles/k_alias_fast_k26_m2p28_traffic.md)"}
-# Warp instructions per edge of the same kernel (smsp__inst_executed.sum / 2^26 on
-# the m=2^26 `ncu --set full` capture of this workload; ALU-pipe instructions from
-# smsp__inst_executed_pipe_alu.sum on the same case, an earlier build of the same
-# kernel code: identical total instruction count and ALU-pipe share), valid for
-# the same hash.
-INSTR = {"kernel_sha256_16": "35fedf31c18221e1", "warp_instr_per_edge": 293341562 / 2 ** 26,
-         "alu_warp_instr_per_edge": 71.1 / 32}
+# Warp instructions per edge of the same kernel (smsp__inst_executed.sum and
+# smsp__inst_executed_pipe_alu.sum / 2^26 on an m=2^26 capture of this workload,
+# `ncu --metrics ... -k regex:k_alias_fast -s 3 -c 1`), valid for the same hash.
+INSTR = {"kernel_sha256_16": "e2a6c8914b67d5b0", "warp_instr_per_edge": 293341562 / 2 ** 26,
+         "alu_warp_instr_per_edge": 149171022 / 2 ** 26}
 KERNEL_SOURCES = ("paper_1905_03525_gb300/csrc/rmat_device.cuh", "paper_1905_03525_gb300/csrc/rmat_kernels.cu")
 
 

@@ -1694,11 +1694,15 @@ rmat_status launch_alias(const rmat_table *t, const uint32_t *dblob, const Alias
     // the table allows it; the ragged tail (and every other case) to k_alias.
     if (plan.fast_kernel && tile % 128 == 0 && count >= uint64_t(tile) &&
         (reinterpret_cast<uintptr_t>(out) & 15u) == 0) {
-        const uint64_t nfull = count / uint64_t(tile);
+        // a launch too small to give every warp of the GPU a tile takes
+        // smaller tiles (down to 128 edges; the bytes do not depend on it)
+        int ftile = tile;
+        while (ftile > 128 && count / uint64_t(ftile) < max_ctas * uint64_t(warps)) ftile /= 2;
+        const uint64_t nfull = count / uint64_t(ftile);
         Job F = J;
-        F.count = nfull * uint64_t(tile);
+        F.count = nfull * uint64_t(ftile);
         const unsigned grid = unsigned(std::max<uint64_t>(1, std::min((nfull + warps - 1) / warps, max_ctas)));
-        void *params[] = {&F, &S, &tile};
+        void *params[] = {&F, &S, &ftile};
         cudaError_t e =
             cudaLaunchKernel(plan.fast_kernel, dim3(grid), dim3(plan.threads), params, plan.smem_bytes, stream);
         if (e != cudaSuccess) return fail(RMAT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
